@@ -1,0 +1,183 @@
+/*
+ * stiles.h -- C ABI of the GB300 (sm_103a) selected-inversion library.
+ *
+ * Computes, for a symmetric positive definite block-arrowhead matrix A,
+ *   (1) the tiled Cholesky factor A = L L^T restricted to the band-plus-arrow
+ *       tile pattern (Sec. III of the sTiles selected-inversion paper,
+ *       arXiv 2504.19171: POTRF / TRSM / SYRK / GEMM on the structurally
+ *       non-zero tiles), and
+ *   (2) the selected inverse Sigma = A^{-1} on exactly the tiles of L
+ *       (Sec. III-B, Fig. 2 case 7: the selection equals L's pattern), by the
+ *       two-phase method: phase 1 (Algorithm 2) inverts each diagonal tile of
+ *       L and scales the off-diagonal tiles, phase 2 (Algorithm 3, with the
+ *       tile recurrences of Sec. III-A) sweeps the tile columns backwards,
+ *   (3) logdet(A) = 2 * sum log diag(L).
+ *
+ * Matrix model. nt band tile columns of order b, lower bandwidth `band`
+ * tiles (w), and an arrow tile row of height `arrow` (a, tile index nt):
+ *   struct(k) = { k+1 .. min(k+w, nt-1) }  U  { nt   if a > 0 },
+ * tile (i,k) is in the pattern iff i == k or i in struct(k). n = nt*b + a.
+ * a = 0 gives a pure block-banded matrix; w = 0 a block-diagonal one.
+ *
+ * Tile layout (the same for A, L and Sigma; "packed band+arrow layout").
+ * Every tile is a dense column-major array whose leading dimension is its
+ * row count (b, or a for arrow tiles). Tile column k < nt occupies the
+ * fixed-stride slot
+ *     colstride = (1 + w) * b * b + a * b            doubles
+ * starting at k * colstride:
+ *     (k,k)       at k*colstride                     b x b
+ *     (k+d,k)     at k*colstride + d*b*b,  1<=d<=w    b x b
+ *     (nt,k)      at k*colstride + (1+w)*b*b          a x b
+ * and the corner (nt,nt) (a x a) sits at nt*colstride. Total doubles:
+ *     stiles_layout_doubles = nt*colstride + a*a.
+ * Sub-diagonal slots with k+d > nt-1 exist but are never read or written.
+ * Input A: only the lower triangle of diagonal tiles is read.
+ * Output L: lower triangle of diagonal tiles; their strict upper triangle
+ * is written as zero. Output Sigma: every entry of every pattern tile,
+ * diagonal tiles full and exactly symmetric.
+ *
+ * Memory ownership. All device buffers (A, L, Sigma, scratch) belong to the
+ * caller (e.g. torch.empty(..., device="cuda")). The handle owns host
+ * metadata, a read-only device task table built at create time, and a small
+ * device status block (status word, logdet partial sums). Launches are
+ * asynchronous on the caller's stream; one handle runs one launch at a time
+ * (its status block and the caller's scratch are per launch).
+ *
+ * Precision. STILES_FP64 computes everything in IEEE binary64 on the FP64
+ * pipe (GB300's tcgen05 tensor cores have no FP64 kind).
+ *
+ * Errors. Every function returns STILES_OK (0) or a negative code. Launch
+ * functions only report argument and CUDA launch errors; numerical status
+ * (NOT_SPD, TIMEOUT) is read with stiles_status / stiles_logdet, which wait
+ * for the last launch of the handle to finish.
+ */
+#ifndef STILES_H
+#define STILES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stiles_handle *stiles_t;
+
+enum stiles_status_code {
+  STILES_OK = 0,
+  STILES_ERR_INVALID_ARG = -1, /* bad shape, null pointer, wrong handle state */
+  STILES_ERR_NOT_SPD = -2,     /* a pivot of POTRF was not positive (or NaN) */
+  STILES_ERR_TIMEOUT = -3,     /* a bounded dependency wait on the device expired */
+  STILES_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  STILES_ERR_OOM = -5,         /* host or device allocation for the handle failed */
+  STILES_ERR_UNSUPPORTED = -6, /* precision or option not available */
+  STILES_ERR_PLAN = -7         /* a task table failed its consistency check */
+};
+
+enum stiles_precision { STILES_FP64 = 0 };
+
+/* Create a handle for one matrix shape.
+ *   nt >= 1 band tile columns, b >= 1 tile order, band = w >= 0 lower tile
+ *   bandwidth (clipped to nt-1), arrow = a >= 0 arrow width,
+ *   precision = STILES_FP64.
+ * Builds the task DAG of the factorization, of the selected inversion and of
+ * both fused (host, C++), orders each by a critical-path list schedule, and
+ * uploads the tables. Returns STILES_ERR_INVALID_ARG for a bad shape,
+ * STILES_ERR_UNSUPPORTED for another precision, STILES_ERR_OOM /
+ * STILES_ERR_CUDA if the tables cannot be placed on the current device.
+ * On success *out owns the handle; release it with stiles_destroy. */
+int stiles_create(int nt, int b, int band, int arrow, int precision, stiles_t *out);
+
+/* Doubles of one packed A / L / Sigma buffer (see the layout above). */
+int stiles_layout_doubles(stiles_t h, size_t *doubles);
+
+/* Bytes the caller must provide: L and Sigma buffers (equal to the packed
+ * size * 8) and a scratch buffer (device, 256-byte aligned) that holds
+ * L_ii^{-1}, the scaled off-diagonal tiles L_ki L_ii^{-1} and the dependency
+ * counters. Any pointer may be NULL to skip it. */
+int stiles_workspace_bytes(stiles_t h, size_t *L_bytes, size_t *sigma_bytes, size_t *scratch_bytes);
+
+/* Tiled Cholesky (Sec. III): reads A_tiles (device, packed layout), writes
+ * L_tiles (device, packed layout). A_tiles and L_tiles may be the same
+ * buffer (in-place factorization). scratch: device, >= scratch_bytes.
+ * One persistent kernel launch on `stream` (a cudaStream_t, NULL = legacy
+ * default stream). Asynchronous: a non-SPD matrix is reported by
+ * stiles_status / stiles_logdet as STILES_ERR_NOT_SPD with the LAPACK-style
+ * 1-based global column of the first failing pivot. */
+int stiles_factor(stiles_t h, const double *A_tiles, double *L_tiles, void *scratch, void *stream);
+
+/* Selected inversion (Algorithms 2 and 3): reads L_tiles (device, output of
+ * stiles_factor, complete before this launch in stream order), writes
+ * Sigma_tiles (device, packed layout; must not alias L_tiles or scratch).
+ * One persistent kernel launch on `stream`; asynchronous. */
+int stiles_selinv(stiles_t h, const double *L_tiles, double *Sigma_tiles, void *scratch, void *stream);
+
+/* Factorization and selected inversion in ONE persistent launch: the phase-1
+ * work of tile column i starts as soon as column i of L is final, while
+ * later columns are still being factored. Same buffers and rules as the two
+ * calls above (A_tiles may alias L_tiles; Sigma_tiles must not alias
+ * either). Asynchronous. */
+int stiles_factor_selinv(stiles_t h, const double *A_tiles, double *L_tiles, double *Sigma_tiles, void *scratch,
+                         void *stream);
+
+/* logdet(A) = 2 * sum log diag(L) from the last factorization of this handle
+ * (stiles_factor or stiles_factor_selinv; a later stiles_selinv does not
+ * change it). Waits for the handle's last launch. Returns that
+ * factorization's status code (STILES_OK, STILES_ERR_NOT_SPD,
+ * STILES_ERR_TIMEOUT), or STILES_ERR_INVALID_ARG if the handle has not
+ * factorized yet; *out_host is written only on STILES_OK. */
+int stiles_logdet(stiles_t h, double *out_host);
+
+/* Device status of the last launch (check it after stiles_factor before
+ * calling stiles_selinv: a selected inversion of a failed factor returns
+ * meaningless values with an OK status). Waits for it, then writes *code (a
+ * stiles_status_code), *info (NOT_SPD: 1-based global column of the first
+ * failing pivot; TIMEOUT: index of the task whose wait expired; else 0) and
+ * *tasks_done (tasks that completed). Any output pointer may be NULL.
+ * Returns STILES_OK if the status could be read. */
+int stiles_status(stiles_t h, int *code, long long *info, long long *tasks_done);
+
+/* Options. STILES_OPT_WAIT_BUDGET_NS: bound of one device dependency wait in
+ * nanoseconds (default 20 s); when it expires the launch stops with
+ * STILES_ERR_TIMEOUT instead of hanging. STILES_OPT_GRID: persistent CTAs per
+ * launch (0 = one per SM). */
+enum stiles_option { STILES_OPT_WAIT_BUDGET_NS = 1, STILES_OPT_GRID = 2 };
+int stiles_set_option(stiles_t h, int option, long long value);
+
+/* Plan statistics for a shape, computed on the host (no GPU, no handle).
+ * which: 0 = factor plan, 1 = selinv plan, 2 = fused plan; workers = number
+ * of persistent workers the list schedule assumes (e.g. the SM count).
+ * stats[0] tasks, [1] segments, [2] waits, [3] counters,
+ * [4] algorithmic flops of the tile operations (POTRF, TRTRI, LAUUM m^3/3;
+ *     TRSM, TRMM m k^2; SYRK and the symmetric Sigma_ii update m^2 k;
+ *     GEMM 2 m n k),
+ * [5] phase-2 tile GEMMs: (tile, tile) products accumulated into Sigma tiles
+ *     (the count of the GEMM-count table of Sec. III-E and Appendix A),
+ * [6] critical path and [7] list-schedule makespan, in estimated ns.
+ * Returns STILES_ERR_INVALID_ARG for a bad shape, STILES_ERR_PLAN if the
+ * table fails its consistency check. */
+int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]);
+
+/* Test hook: build the plan `which` for a shape, corrupt its dependency table
+ * on the host (mode 1: one wait names a counter beyond the table; mode 2: one
+ * wait needs one more signal than exists; mode 3: a wait on a task later in
+ * claim order) and return the consistency check's verdict (expected
+ * STILES_ERR_PLAN). Host only. */
+int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode);
+
+/* Test hook: make the handle's plan `which` unsatisfiable on the device (the
+ * last task waits for a counter that no task signals) without the host check,
+ * so that a launch must end with STILES_ERR_TIMEOUT once the wait budget
+ * expires. Used to test that a stuck dependency ends the kernel cleanly. */
+int stiles_debug_break_plan(stiles_t h, int which);
+
+/* Release the handle (waits for its last launch). Accepts NULL. */
+int stiles_destroy(stiles_t h);
+
+/* Human-readable name of a status code. */
+const char *stiles_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STILES_H */

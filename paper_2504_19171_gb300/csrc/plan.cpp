@@ -1,0 +1,618 @@
+// Host planner: expands the tile DAG of the tiled Cholesky and of the
+// two-phase selected inversion into fine-block tasks, then orders them by a
+// critical-path-first list schedule.
+//
+// Tile-level method (sTiles selected inversion, arXiv 2504.19171):
+//   factor  (Sec. III)       for k: L_kk = POTRF(A_kk); L_ik = A_ik L_kk^{-T};
+//                            A_ij -= L_ik L_jk^T for i >= j in struct(k)
+//   phase 1 (Algorithm 2)    Linv_ii = L_ii^{-1} ("TRSM against I");
+//                            Sigma_ii^0 = Linv_ii^T Linv_ii (LAUUM);
+//                            U_ki = L_ki Linv_ii (TRMM), k in struct(i)
+//   phase 2 (Algorithm 3,    for i descending: Sigma_ji = -sum_k S_jk U_ki,
+//            Sec. III-A)     j in struct(i) (S_jk = Sigma_jk or Sigma_kj^T);
+//                            Sigma_ii = Sigma_ii^0 - sum_k Sigma_ki^T U_ki
+// Each tile operation is split over FB x FB output blocks so that one b x b
+// tile operation occupies many SMs at once; the per-block work is a K-loop
+// over contiguous panels of other tiles (a "segment").
+//
+// The factorization runs at fine-block granularity in right-looking order
+// (every b x b POTRF/TRSM/SYRK/GEMM decomposes exactly into FB-block POTRF,
+// TRSM and GEMM updates), which keeps the critical path at about three small
+// block operations per FB columns. Updates into one block are applied by a
+// chain of tasks (increasing source column); the last update of a diagonal
+// block is fused into its POTRF.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <functional>
+#include <queue>
+
+#include "../../include/stiles.h"
+
+namespace stiles {
+namespace {
+
+// Cost model for the list schedule (one worker = one SM of a GB300 at about
+// 1.9 GHz with 2 FP64 FMA per clock): ~7.6 flop/ns, plus a per-task overhead.
+constexpr double kFlopPerNs = 7.6;
+constexpr double kTaskOverheadNs = 2500.0;
+constexpr double kSweepStepNs = 120.0;  // one step of an in-shared-memory triangular sweep
+
+struct Builder {
+  Shape s;
+  Layout L;
+  PlanKind kind;
+  Plan* out;
+  // per emitted task (emission order is topological)
+  std::vector<Task> tasks;
+  std::vector<double> cost;
+  std::vector<std::vector<Seg>> tsegs;
+  std::vector<std::vector<Wait>> twaits;
+  std::vector<std::vector<int32_t>> tsigs;
+  // counters
+  std::vector<char> chain;                    // 1: writers strictly ordered
+  std::vector<std::vector<int32_t>> writers;  // emission ids in signal order
+  double flops = 0;
+  long long tile_gemms = 0;
+  int ndiag = 0;
+
+  Builder(const Shape& sh, PlanKind k, Plan* o) : s(sh), L(sh), kind(k), out(o) {}
+
+  int32_t newctr(bool is_chain) {
+    chain.push_back(is_chain ? 1 : 0);
+    writers.emplace_back();
+    return (int32_t)chain.size() - 1;
+  }
+
+  int emit(Task t, std::vector<Seg> segs, std::vector<Wait> waits, std::vector<int32_t> sigs, double epi_ns) {
+    double f = 0;
+    for (const Seg& g : segs) f += 2.0 * t.m * t.n * g.k;
+    int id = (int)tasks.size();
+    tasks.push_back(t);
+    cost.push_back(kTaskOverheadNs + f / kFlopPerNs + epi_ns);
+    tsegs.push_back(std::move(segs));
+    twaits.push_back(std::move(waits));
+    for (int32_t c : sigs) writers[c].push_back(id);
+    tsigs.push_back(std::move(sigs));
+    return id;
+  }
+
+  static Task blank(uint8_t op, int m, int n) {
+    Task t{};
+    t.out = t.cin = t.aux = -1;
+    t.op = op;
+    t.m = (int16_t)m;
+    t.n = (int16_t)n;
+    t.diag = -1;
+    return t;
+  }
+
+  static Seg seg(int64_t a, int lda, int64_t b, int ldb, int k, bool ta, bool tb) {
+    Seg g;
+    g.a = a; g.b = b; g.lda = lda; g.ldb = ldb; g.k = k;
+    g.trans = (ta ? 1 : 0) | (tb ? 2 : 0);
+    return g;
+  }
+
+  // ------------------------------------------------------------ factor ----
+  // Fine rows are (tile, block row) pairs; a fine column is (tile k, block c).
+  // Counter ids of L blocks: lctr[k][i-slot][r][c] flattened.
+  std::vector<int32_t> lctr;       // per L block (lower pattern)
+  std::vector<int64_t> lctr_base;  // per (i,k) tile: first index into lctr, or -1
+  std::vector<int32_t> lfinal;     // per L block: number of writers (updates + final)
+  std::vector<int32_t> colfinal;   // fused: per tile column, counter of "L column final"
+  std::vector<int32_t> colblocks;  // fused: number of L blocks per tile column
+
+  int tile_slot(int i, int k) const {  // 0 = diag, 1..w = band, w+1 = arrow
+    if (i == k) return 0;
+    if (i == s.nt) return s.w + 1;
+    return i - k;
+  }
+  int64_t& tbase(int i, int k) { return lctr_base[(size_t)k * (s.w + 2) + tile_slot(i, k)]; }
+  int32_t lidx(int i, int k, int r, int c) { return (int32_t)(tbase(i, k) + (int64_t)r * L.nblk(k) + c); }
+
+  void alloc_lblocks() {
+    int cols = L.last() + 1;
+    lctr_base.assign((size_t)cols * (s.w + 2), -1);
+    std::vector<int> st;
+    int64_t nb = 0;
+    for (int k = 0; k < cols; ++k) {
+      tbase(k, k) = nb;
+      nb += (int64_t)L.nblk(k) * L.nblk(k);
+      L.structure(k, st);
+      for (int i : st) {
+        tbase(i, k) = nb;
+        nb += (int64_t)L.nblk(i) * L.nblk(k);
+      }
+    }
+    lctr.assign(nb, -1);
+    lfinal.assign(nb, 0);
+  }
+
+  void build_factor() {
+    alloc_lblocks();
+    std::vector<int> st, stk;
+    int cols = L.last() + 1;
+    // count writers: updates per block + 1 final; and create chain counters
+    if (kind == PLAN_FUSED) {
+      colfinal.resize(cols);
+      colblocks.assign(cols, 0);
+      for (int k = 0; k < cols; ++k) colfinal[k] = newctr(false);
+    }
+    for (int k = 0; k < cols; ++k) {
+      L.structure(k, st);
+      std::vector<int> rows_i;  // tiles in this column: k and struct(k)
+      rows_i.push_back(k);
+      for (int i : st) rows_i.push_back(i);
+      for (int i : rows_i)
+        for (int r = 0; r < L.nblk(i); ++r)
+          for (int c = 0; c < L.nblk(k); ++c) {
+            if (i == k && r < c) continue;
+            lctr[lidx(i, k, r, c)] = newctr(true);
+            if (kind == PLAN_FUSED) colblocks[k]++;
+          }
+    }
+    // emit per fine column q = (kq, cq) in order: the chains into each block
+    // of that column, then its final POTRF / TRSM.
+    for (int kq = 0; kq < cols; ++kq) {
+      L.structure(kq, st);
+      std::vector<int> tiles_below;  // tiles i of column kq: kq itself, then struct(kq)
+      tiles_below.push_back(kq);
+      for (int i : st) tiles_below.push_back(i);
+      for (int cq = 0; cq < L.nblk(kq); ++cq) {
+        for (int i : tiles_below)
+          for (int r = (i == kq ? cq : 0); r < L.nblk(i); ++r) emit_block_chain(i, r, kq, cq);
+      }
+    }
+  }
+
+  // Source tile columns k < kq that update blocks (i, kq): kq and i both in
+  // struct(k).
+  void sources(int i, int kq, std::vector<int>& ks) {
+    ks.clear();
+    int k0 = kq - s.w;
+    if (kq == s.nt) k0 = 0;  // the corner receives from every band column
+    if (k0 < 0) k0 = 0;
+    for (int k = k0; k < kq; ++k) {
+      bool kq_in = (kq == s.nt) ? (s.a > 0) : (kq <= k + L.nsub(k));
+      bool i_in = (i == s.nt) ? (s.a > 0) : (i <= k + L.nsub(k));
+      if (kq_in && i_in) ks.push_back(k);
+    }
+  }
+
+  void emit_block_chain(int i, int r, int kq, int cq) {
+    const int m = L.bdim(i, r), n = L.bdim(kq, cq);
+    const bool diag = (i == kq && r == cq);
+    const int32_t me = lctr[lidx(i, kq, r, cq)];
+    // terms: list of (source tile column k, first block c0, last block c1)
+    struct Term { int k, c0, c1; };
+    std::vector<Term> terms;
+    std::vector<int> ks;
+    sources(i, kq, ks);
+    // Updates from tile columns older than kq-1 were final long before this
+    // block is due: batch them (kChunkOld block columns per task). Updates from
+    // tile column kq-1 and from kq itself arrive one block column at a time
+    // along the critical path: one block column per task.
+    const int kChunkOld = 8;
+    for (int k : ks) {
+      const int step = (k < kq - 1) ? kChunkOld : 1;
+      for (int c0 = 0; c0 < L.nblk(k); c0 += step) terms.push_back({k, c0, std::min(L.nblk(k), c0 + step) - 1});
+    }
+    for (int c = 0; c < cq; ++c) terms.push_back({kq, c, c});  // same tile column: one block column per task
+    const int64_t outref = mkref(BUF_L, L.blk(i, kq, r, cq));
+    const int ld_i = L.rows(i);
+    int nwritten = 0;
+    auto term_seg = [&](const Term& t) {
+      int64_t a = mkref(BUF_L, L.blk(i, t.k, r, t.c0));
+      int64_t b = mkref(BUF_L, L.blk(kq, t.k, cq, t.c0));
+      int kk = std::min(L.rows(t.k), (t.c1 + 1) * FB) - t.c0 * FB;
+      return seg(a, ld_i, b, L.rows(kq), kk, false, true);
+    };
+    auto term_waits = [&](const Term& t, std::vector<Wait>& w) {
+      w.push_back({lctr[lidx(i, t.k, r, t.c1)], lfinal[lidx(i, t.k, r, t.c1)]});
+      w.push_back({lctr[lidx(kq, t.k, cq, t.c1)], lfinal[lidx(kq, t.k, cq, t.c1)]});
+    };
+    size_t nfused = diag && !terms.empty() ? 1 : 0;  // POTRF absorbs its last update
+    size_t nchain = terms.size() - nfused;
+    int total_writers = (int)nchain + 1;
+    lfinal[lidx(i, kq, r, cq)] = total_writers;
+    for (size_t t = 0; t < nchain; ++t) {
+      Task tk = blank(OP_UPD, m, n);
+      tk.out = outref;
+      tk.ldo = ld_i;
+      tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
+      tk.ldc = ld_i;
+      std::vector<Wait> w;
+      if (nwritten > 0) w.push_back({me, nwritten});
+      term_waits(terms[t], w);
+      emit(tk, {term_seg(terms[t])}, w, {me}, 0.0);
+      ++nwritten;
+    }
+    // final task
+    std::vector<Seg> segs;
+    std::vector<Wait> w;
+    if (nwritten > 0) w.push_back({me, nwritten});
+    for (size_t t = nchain; t < terms.size(); ++t) {
+      segs.push_back(term_seg(terms[t]));
+      term_waits(terms[t], w);
+    }
+    Task tk = blank(diag ? OP_POTRF : OP_TRSM_RLT, m, n);
+    tk.out = outref;
+    tk.ldo = ld_i;
+    tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
+    tk.ldc = ld_i;
+    std::vector<int32_t> sig{me};
+    double epi;
+    if (diag) {
+      tk.diag = ndiag++;
+      tk.zrows = cq * FB;
+      tk.gcol = kq * s.b + cq * FB;
+      epi = 3.0 * m * kSweepStepNs;
+    } else {
+      const int32_t dctr = lctr[lidx(kq, kq, cq, cq)];
+      w.push_back({dctr, lfinal[lidx(kq, kq, cq, cq)]});
+      tk.aux = mkref(BUF_L, L.blk(kq, kq, cq, cq));
+      tk.ldx = L.rows(kq);
+      epi = 2.0 * n * kSweepStepNs;
+    }
+    if (kind == PLAN_FUSED) sig.push_back(colfinal[kq]);
+    emit(tk, segs, w, sig, epi);
+  }
+
+  // ------------------------------------------------------------ selinv ----
+  // Counters: Linv column panels (chain), Sigma^0 blocks (chain), U column
+  // panels, Sigma row / column panels (diagonal tiles: lower blocks only).
+  std::vector<int32_t> linv_col;   // [i][c]
+  std::vector<int64_t> linv_base;
+  std::vector<int32_t> s0_ctr;     // [i][r][c] lower
+  std::vector<int64_t> s0_base;
+  std::vector<int32_t> u_col;      // per (k,i) tile: column panels
+  std::vector<int32_t> s_row, s_col;  // per Sigma tile: row / column panels
+  std::vector<int64_t> ut_base, st_rbase, st_cbase;  // indexed by tile slot like lctr_base
+
+  int64_t slot_index(int i, int k) const { return (int64_t)k * (s.w + 2) + tile_slot(i, k); }
+
+  void build_selinv() {
+    const int cols = L.last() + 1;
+    std::vector<int> st;
+    linv_base.assign(cols, 0);
+    s0_base.assign(cols, 0);
+    ut_base.assign((size_t)cols * (s.w + 2), -1);
+    st_rbase.assign((size_t)cols * (s.w + 2), -1);
+    st_cbase.assign((size_t)cols * (s.w + 2), -1);
+    for (int i = 0; i < cols; ++i) {
+      const int R = L.nblk(i);
+      linv_base[i] = linv_col.size();
+      for (int c = 0; c < R; ++c) linv_col.push_back(newctr(true));
+      s0_base[i] = s0_ctr.size();
+      for (int r = 0; r < R; ++r)
+        for (int c = 0; c <= r; ++c) s0_ctr.push_back(newctr(true));
+      // Sigma diag tile panels
+      st_rbase[slot_index(i, i)] = s_row.size();
+      for (int r = 0; r < R; ++r) s_row.push_back(newctr(false));
+      st_cbase[slot_index(i, i)] = s_col.size();
+      for (int c = 0; c < R; ++c) s_col.push_back(newctr(false));
+      L.structure(i, st);
+      for (int k : st) {
+        ut_base[slot_index(k, i)] = u_col.size();
+        for (int c = 0; c < R; ++c) u_col.push_back(newctr(false));
+        st_rbase[slot_index(k, i)] = s_row.size();
+        for (int r = 0; r < L.nblk(k); ++r) s_row.push_back(newctr(false));
+        st_cbase[slot_index(k, i)] = s_col.size();
+        for (int c = 0; c < R; ++c) s_col.push_back(newctr(false));
+      }
+    }
+    for (int i = 0; i < cols; ++i) emit_phase1(i);
+    for (int i = cols - 1; i >= 0; --i) emit_phase2(i);
+  }
+
+  int32_t linv_ctr(int i, int c) const { return linv_col[linv_base[i] + c]; }
+  int32_t s0(int i, int r, int c) const { return s0_ctr[s0_base[i] + (int64_t)r * (r + 1) / 2 + c]; }
+  int32_t ucol(int k, int i, int c) const { return u_col[ut_base[slot_index(k, i)] + c]; }
+  int32_t srow(int j, int i, int r) const { return s_row[st_rbase[slot_index(j, i)] + r]; }
+  int32_t scol(int j, int i, int c) const { return s_col[st_cbase[slot_index(j, i)] + c]; }
+
+  void add_fused_wait(int i, std::vector<Wait>& w) {
+    if (kind == PLAN_FUSED) w.push_back({colfinal[i], colblocks[i]});
+  }
+
+  void emit_phase1(int i) {
+    const int R = L.nblk(i), ld = L.rows(i);
+    std::vector<int> st;
+    // TRTRI of the diagonal tile, block column by block column
+    for (int c = 0; c < R; ++c) {
+      for (int r = c; r < R; ++r) {
+        const int m = L.bdim(i, r), n = L.bdim(i, c);
+        std::vector<Wait> w;
+        add_fused_wait(i, w);
+        if (r == c) {
+          Task t = blank(OP_TRTRI, m, n);
+          t.out = mkref(BUF_W, L.blk(i, i, r, c));
+          t.ldo = ld;
+          t.aux = mkref(BUF_L, L.blk(i, i, r, r));
+          t.ldx = ld;
+          emit(t, {}, w, {linv_ctr(i, c)}, 2.0 * m * kSweepStepNs);
+        } else {
+          // Linv[r,c] = -L[r,r]^{-1} sum_{q=c}^{r-1} L[r,q] Linv[q,c]
+          Task t = blank(OP_TRSM_LLN, m, n);
+          t.out = mkref(BUF_W, L.blk(i, i, r, c));
+          t.ldo = ld;
+          t.aux = mkref(BUF_L, L.blk(i, i, r, r));
+          t.ldx = ld;
+          w.push_back({linv_ctr(i, c), r - c});
+          Seg g = seg(mkref(BUF_L, L.blk(i, i, r, c)), ld, mkref(BUF_W, L.blk(i, i, c, c)), ld, (r - c) * FB, false,
+                      false);
+          emit(t, {g}, w, {linv_ctr(i, c)}, 2.0 * m * kSweepStepNs);
+        }
+      }
+    }
+    // LAUUM: Sigma^0[r,c] = sum_{q>=r} Linv[q,r]^T Linv[q,c], r >= c
+    for (int r = 0; r < R; ++r)
+      for (int c = 0; c <= r; ++c) {
+        const int m = L.bdim(i, r), n = L.bdim(i, c);
+        Task t = blank(OP_STORE, m, n);
+        t.out = mkref(BUF_S, L.blk(i, i, r, c));
+        t.ldo = ld;
+        std::vector<Wait> w{{linv_ctr(i, r), R - r}, {linv_ctr(i, c), R - c}};
+        Seg g = seg(mkref(BUF_W, L.blk(i, i, r, r)), ld, mkref(BUF_W, L.blk(i, i, r, c)), ld, ld - r * FB, true,
+                    false);
+        emit(t, {g}, w, {s0(i, r, c)}, 0.0);
+      }
+    // TRMM: U_ki = L_ki Linv_ii
+    L.structure(i, st);
+    for (int k : st) {
+      const int ldk = L.rows(k);
+      for (int c = 0; c < R; ++c)
+        for (int r = 0; r < L.nblk(k); ++r) {
+          const int m = L.bdim(k, r), n = L.bdim(i, c);
+          Task t = blank(OP_STORE, m, n);
+          t.out = mkref(BUF_W, L.blk(k, i, r, c));
+          t.ldo = ldk;
+          std::vector<Wait> w;
+          add_fused_wait(i, w);
+          w.push_back({linv_ctr(i, c), R - c});
+          Seg g = seg(mkref(BUF_L, L.blk(k, i, r, c)), ldk, mkref(BUF_W, L.blk(i, i, c, c)), ld, ld - c * FB, false,
+                      false);
+          emit(t, {g}, w, {ucol(k, i, c)}, 0.0);
+        }
+    }
+  }
+
+  void emit_phase2(int i) {
+    const int R = L.nblk(i), ld = L.rows(i);
+    std::vector<int> st;
+    L.structure(i, st);
+    // off-diagonal tiles, j from the last down (Algorithm 3's j loop)
+    for (int tj = (int)st.size() - 1; tj >= 0; --tj) {
+      const int j = st[tj], ldj = L.rows(j);
+      for (int c = 0; c < R; ++c)
+        for (int r = 0; r < L.nblk(j); ++r) {
+          const int m = L.bdim(j, r), n = L.bdim(i, c);
+          Task t = blank(OP_NEG, m, n);
+          t.out = mkref(BUF_S, L.blk(j, i, r, c));
+          t.ldo = ldj;
+          std::vector<Seg> segs;
+          std::vector<Wait> w;
+          for (int k : st) {
+            const int ldk = L.rows(k);
+            if (j == k) {
+              segs.push_back(seg(mkref(BUF_S, L.blk(j, j, r, 0)), ldj, mkref(BUF_W, L.blk(k, i, 0, c)), ldk, ldk,
+                                 false, false));
+              w.push_back({srow(j, j, r), r + 1});
+              w.push_back({scol(j, j, r), L.nblk(j) - r});
+            } else if (j > k) {
+              segs.push_back(seg(mkref(BUF_S, L.blk(j, k, r, 0)), ldj, mkref(BUF_W, L.blk(k, i, 0, c)), ldk, ldk,
+                                 false, false));
+              w.push_back({srow(j, k, r), L.nblk(k)});
+            } else {
+              segs.push_back(seg(mkref(BUF_S, L.blk(k, j, 0, r)), ldk, mkref(BUF_W, L.blk(k, i, 0, c)), ldk, ldk,
+                                 true, false));
+              w.push_back({scol(k, j, r), L.nblk(k)});
+            }
+            w.push_back({ucol(k, i, c), L.nblk(k)});
+          }
+          emit(t, segs, w, {srow(j, i, r), scol(j, i, c)}, 0.0);
+        }
+      tile_gemms += (long long)st.size();
+    }
+    // diagonal tile: Sigma_ii = Sigma^0 - sum_k Sigma_ki^T U_ki (lower blocks, mirrored)
+    for (int r = 0; r < R; ++r)
+      for (int c = 0; c <= r; ++c) {
+        const int m = L.bdim(i, r), n = L.bdim(i, c);
+        Task t = blank(OP_SYMUPD, m, n);
+        t.out = mkref(BUF_S, L.blk(i, i, r, c));
+        t.ldo = ld;
+        t.cin = t.out;
+        t.ldc = ld;
+        if (r != c) {
+          t.aux = mkref(BUF_S, L.blk(i, i, c, r));
+          t.ldx = ld;
+        } else {
+          t.flags = 1;
+        }
+        std::vector<Seg> segs;
+        std::vector<Wait> w{{s0(i, r, c), 1}};
+        for (int k : st) {
+          const int ldk = L.rows(k);
+          segs.push_back(seg(mkref(BUF_S, L.blk(k, i, 0, r)), ldk, mkref(BUF_W, L.blk(k, i, 0, c)), ldk, ldk, true,
+                             false));
+          w.push_back({scol(k, i, r), L.nblk(k)});
+          w.push_back({ucol(k, i, c), L.nblk(k)});
+        }
+        emit(t, segs, w, {srow(i, i, r), scol(i, i, c)}, 0.0);
+      }
+    tile_gemms += (long long)st.size();
+  }
+
+  // ---------------------------------------------------------- schedule ----
+  int finish(int workers) {
+    const int nt_ = (int)tasks.size();
+    // predecessor edges from waits
+    std::vector<std::vector<int32_t>> succ(nt_);
+    std::vector<int32_t> indeg(nt_, 0);
+    for (int t = 0; t < nt_; ++t) {
+      std::vector<int32_t> preds;
+      for (const Wait& w : twaits[t]) {
+        const auto& wr = writers[w.ctr];
+        if (w.need > (int)wr.size() || w.need < 0) return STILES_ERR_PLAN;
+        if (w.need == 0) continue;
+        if (chain[w.ctr]) preds.push_back(wr[w.need - 1]);
+        else for (int q = 0; q < w.need; ++q) preds.push_back(wr[q]);
+      }
+      std::sort(preds.begin(), preds.end());
+      preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
+      for (int32_t p : preds) {
+        if (p >= t) return STILES_ERR_PLAN;  // emission order must be topological
+        succ[p].push_back(t);
+        indeg[t]++;
+      }
+    }
+    // bottom levels
+    std::vector<double> blevel(nt_, 0.0);
+    double cp = 0;
+    for (int t = nt_ - 1; t >= 0; --t) {
+      double best = 0;
+      for (int32_t q : succ[t]) best = std::max(best, blevel[q]);
+      blevel[t] = cost[t] + best;
+      cp = std::max(cp, blevel[t]);
+    }
+    // list schedule: free workers take the ready task with the largest bottom level
+    using RItem = std::pair<double, int32_t>;
+    std::priority_queue<RItem> ready;
+    using EItem = std::pair<double, int32_t>;  // (finish time, task)
+    std::priority_queue<EItem, std::vector<EItem>, std::greater<EItem>> running;
+    for (int t = 0; t < nt_; ++t)
+      if (indeg[t] == 0) ready.push({blevel[t], t});
+    std::vector<int32_t> order;
+    order.reserve(nt_);
+    double now = 0;
+    int free_workers = std::max(1, workers);
+    while ((int)order.size() < nt_) {
+      while (free_workers > 0 && !ready.empty()) {
+        int32_t t = ready.top().second;
+        ready.pop();
+        order.push_back(t);
+        running.push({now + cost[t], t});
+        --free_workers;
+      }
+      if (running.empty()) return STILES_ERR_PLAN;  // cycle
+      EItem e = running.top();
+      running.pop();
+      now = e.first;
+      ++free_workers;
+      for (int32_t q : succ[e.second])
+        if (--indeg[q] == 0) ready.push({blevel[q], q});
+      while (!running.empty() && running.top().first <= now) {
+        EItem e2 = running.top();
+        running.pop();
+        ++free_workers;
+        for (int32_t q : succ[e2.second])
+          if (--indeg[q] == 0) ready.push({blevel[q], q});
+      }
+    }
+    while (!running.empty()) { now = std::max(now, running.top().first); running.pop(); }
+    // write the plan in claim order
+    Plan& p = *out;
+    p.tasks.clear(); p.segs.clear(); p.waits.clear(); p.sigs.clear();
+    p.tasks.reserve(nt_);
+    for (int32_t t : order) {
+      Task tk = tasks[t];
+      tk.seg0 = (int32_t)p.segs.size();
+      tk.nseg = (int32_t)tsegs[t].size();
+      for (const Seg& g : tsegs[t]) p.segs.push_back(g);
+      tk.wait0 = (int32_t)p.waits.size();
+      tk.nwait = (int32_t)twaits[t].size();
+      for (const Wait& w : twaits[t]) p.waits.push_back(w);
+      tk.sig0 = (int32_t)p.sigs.size();
+      tk.nsig = (int16_t)tsigs[t].size();
+      for (int32_t c : tsigs[t]) p.sigs.push_back(c);
+      p.tasks.push_back(tk);
+    }
+    p.nctr = (int32_t)chain.size();
+    p.ndiag = ndiag;
+    p.flops = flops;
+    p.tile_gemms = tile_gemms;
+    p.cp_ns = cp;
+    p.makespan_ns = now;
+    return 0;
+  }
+};
+
+}  // namespace
+
+// Algorithmic flops of the tile operations (the counting convention used for
+// every TFLOP/s figure): POTRF, TRTRI, LAUUM m^3/3; TRSM, TRMM m k^2;
+// SYRK m^2 k; GEMM 2 m n k; the symmetric Sigma_ii update m^2 k per term
+// (only its lower triangle is computed, like SYRK).
+double tile_flops(const Shape& s, PlanKind kind) {
+  Layout L(s);
+  std::vector<int> st;
+  double f = 0;
+  const int cols = L.last() + 1;
+  for (int k = 0; k < cols; ++k) {
+    const double mk = L.rows(k);
+    L.structure(k, st);
+    if (kind != PLAN_SELINV) {
+      f += mk * mk * mk / 3.0;                          // POTRF
+      for (size_t t = 0; t < st.size(); ++t) {
+        const double mi = L.rows(st[t]);
+        f += mi * mk * mk;                              // TRSM
+        f += mi * mi * mk;                              // SYRK
+        for (size_t u = 0; u < t; ++u) f += 2.0 * mi * L.rows(st[u]) * mk;  // GEMM
+      }
+    }
+    if (kind != PLAN_FACTOR) {
+      f += 2.0 * mk * mk * mk / 3.0;                    // TRTRI + LAUUM
+      for (int j : st) {
+        const double mj = L.rows(j);
+        f += mj * mk * mk;                              // TRMM
+        for (int q : st) f += 2.0 * mj * mk * L.rows(q);  // Sigma_jk U_ki
+        f += mk * mk * mj;                              // Sigma_kk update
+      }
+    }
+  }
+  return f;
+}
+
+int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out) {
+  if (s.nt < 1 || s.b < 1 || s.w < 0 || s.a < 0 || s.w > s.nt - 1) return STILES_ERR_INVALID_ARG;
+  // Task-table size guard: about (1+w+1) tiles per column, nblk^2 blocks per
+  // tile and up to (w+1)*nblk + nblk chain tasks per block.
+  const double nb = (s.b + FB - 1) / FB, na = (s.a + FB - 1) / FB;
+  const double est = (double)s.nt * (s.w + 2) * nb * (nb + na) * ((s.w + 2) * nb + 8);
+  if (est > 4.0e8) return STILES_ERR_INVALID_ARG;
+  Builder B(s, kind, out);
+  if (kind == PLAN_FACTOR || kind == PLAN_FUSED) B.build_factor();
+  if (kind == PLAN_SELINV || kind == PLAN_FUSED) B.build_selinv();
+  B.flops = tile_flops(s, kind);
+  int rc = B.finish(workers);
+  if (rc) return rc;
+  return check_plan(*out);
+}
+
+int check_plan(const Plan& p) {
+  const int64_t ntasks = (int64_t)p.tasks.size();
+  std::vector<int32_t> seen(p.nctr, 0);  // signals issued by tasks before the current one
+  for (int64_t t = 0; t < ntasks; ++t) {
+    const Task& tk = p.tasks[t];
+    if (tk.wait0 < 0 || tk.nwait < 0 || (int64_t)tk.wait0 + tk.nwait > (int64_t)p.waits.size()) return STILES_ERR_PLAN;
+    if (tk.seg0 < 0 || tk.nseg < 0 || (int64_t)tk.seg0 + tk.nseg > (int64_t)p.segs.size()) return STILES_ERR_PLAN;
+    if (tk.sig0 < 0 || tk.nsig < 0 || (int64_t)tk.sig0 + tk.nsig > (int64_t)p.sigs.size()) return STILES_ERR_PLAN;
+    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_SYMUPD) return STILES_ERR_PLAN;
+    for (int q = 0; q < tk.nwait; ++q) {
+      const Wait& w = p.waits[tk.wait0 + q];
+      if (w.ctr < 0 || w.ctr >= p.nctr) return STILES_ERR_PLAN;
+      if (w.need > seen[w.ctr]) return STILES_ERR_PLAN;  // would wait for a later task: can deadlock
+    }
+    for (int q = 0; q < tk.nsig; ++q) {
+      int32_t c = p.sigs[tk.sig0 + q];
+      if (c < 0 || c >= p.nctr) return STILES_ERR_PLAN;
+      seen[c]++;
+    }
+  }
+  return 0;
+}
+
+}  // namespace stiles

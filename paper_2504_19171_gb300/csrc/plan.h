@@ -1,0 +1,133 @@
+// Task tables shared by the host planner (plan.cpp) and the persistent
+// kernel (stiles_kernel.cu).
+//
+// A plan is a flat list of fine-block tasks in claim order. Every task writes
+// one output block of at most FB x FB doubles:
+//     acc = sum over its segments  op(A_s) * op(B_s)          (FP64)
+// followed by an epilogue (Op) that combines acc with an input block and, for
+// POTRF / TRSM / TRTRI, a triangular solve in shared memory. The paper's tile
+// operations (Sec. III-A; Algorithms 2 and 3) are split into such tasks over
+// FB x FB sub-blocks of the b x b tiles.
+//
+// Dependencies are counters in device memory: a task lists (counter, need)
+// pairs to wait for and the counters it increments when done (the producer /
+// consumer flags of Algorithm 3, one per block or block panel instead of one
+// per tile).
+#pragma once
+#include <stdint.h>
+
+namespace stiles {
+
+constexpr int FB = 64;  // fine block order (rows and columns of one task's output)
+
+// Buffer ids, stored in the top bits of a 64-bit element offset.
+enum Buf : int { BUF_A = 0, BUF_L = 1, BUF_S = 2, BUF_W = 3 };
+constexpr int BUF_SHIFT = 60;
+constexpr int64_t OFF_MASK = (int64_t(1) << BUF_SHIFT) - 1;
+inline int64_t mkref(int buf, int64_t off) { return (int64_t(buf) << BUF_SHIFT) | off; }
+
+enum Op : uint8_t {
+  OP_UPD = 0,       // out = cin - acc
+  OP_POTRF = 1,     // out = chol(cin - acc)           (square, lower; zero above the diagonal)
+  OP_TRSM_RLT = 2,  // out = (cin - acc) * T^{-T}      (T = aux, lower n x n)
+  OP_TRTRI = 3,     // out = T^{-1}                    (T = aux, lower m x m; zero above)
+  OP_TRSM_LLN = 4,  // out = -T^{-1} * acc             (T = aux, lower m x m)
+  OP_STORE = 5,     // out = acc
+  OP_NEG = 6,       // out = -acc
+  OP_SYMUPD = 7,    // out = cin - acc and its transpose into the mirror block (aux)
+};
+
+struct Seg {       // acc += op(A) (m x k) * op(B) (k x n)
+  int64_t a, b;    // buffer refs (mkref) of element (0,0) of the stored operands
+  int32_t lda, ldb;
+  int32_t k;       // inner length
+  int32_t trans;   // bit 0: op(A) = A^T ; bit 1: op(B) = B^T
+};
+
+struct Wait {
+  int32_t ctr;
+  int32_t need;    // wait until counter >= need
+};
+
+struct Task {        // 64 bytes
+  int64_t out;       // ref of the output block
+  int64_t cin;       // ref of the input block (OP_UPD/POTRF/TRSM_RLT/SYMUPD) or -1
+  int64_t aux;       // ref of the triangular block (TRSM/TRTRI) or the mirror block (SYMUPD) or -1
+  int32_t ldo, ldc, ldx;
+  int16_t m, n;      // output rows / columns (<= FB)
+  int32_t seg0, nseg;
+  int32_t wait0, nwait;
+  int32_t sig0;      // signals: sig[sig0 .. sig0+nsig)
+  int16_t nsig;
+  uint8_t op;
+  uint8_t flags;     // bit 0: SYMUPD on a diagonal block (mirror inside the block)
+  int32_t diag;      // POTRF: index of its logdet partial sum
+  int32_t zrows;     // POTRF: rows above the block in its tile column to zero (L's strict upper part)
+  int32_t gcol;      // POTRF: 0-based global column of the block's first pivot
+};
+static_assert(sizeof(Task) == 80, "task layout");
+
+}  // namespace stiles
+
+#ifndef __CUDACC_RTC__
+#include <vector>
+
+namespace stiles {
+
+enum PlanKind : int { PLAN_FACTOR = 0, PLAN_SELINV = 1, PLAN_FUSED = 2 };
+
+struct Shape {
+  int nt, b, w, a;  // w already clipped to nt-1
+};
+
+struct Plan {
+  std::vector<Task> tasks;  // in claim order
+  std::vector<Seg> segs;
+  std::vector<Wait> waits;
+  std::vector<int32_t> sigs;
+  int32_t nctr = 0;         // dependency counters used
+  int32_t ndiag = 0;        // logdet partial sums (one per POTRF task)
+  double flops = 0;         // algorithmic flops (tile-operation convention)
+  long long tile_gemms = 0; // phase-2 (tile, tile) products
+  double cp_ns = 0;         // critical path of the estimated task graph
+  double makespan_ns = 0;   // list-schedule makespan on `workers` workers
+};
+
+// Packed band+arrow layout (see include/stiles.h).
+struct Layout {
+  int nt, b, w, a;
+  int64_t colstride;
+  explicit Layout(const Shape& s)
+      : nt(s.nt), b(s.b), w(s.w), a(s.a), colstride((int64_t)(1 + s.w) * s.b * s.b + (int64_t)s.a * s.b) {}
+  int rows(int i) const { return i == nt ? a : b; }
+  int last() const { return a > 0 ? nt : nt - 1; }
+  int nsub(int k) const { return k >= nt ? 0 : (nt - 1 - k < w ? nt - 1 - k : w); }
+  int64_t doubles() const { return (int64_t)nt * colstride + (int64_t)a * a; }
+  int64_t tile(int i, int k) const {
+    if (k == nt) return (int64_t)nt * colstride;
+    if (i == nt) return (int64_t)k * colstride + (int64_t)(1 + w) * b * b;
+    return (int64_t)k * colstride + (int64_t)(i - k) * b * b;
+  }
+  int nblk(int i) const { return (rows(i) + FB - 1) / FB; }
+  int bdim(int i, int r) const { int m = rows(i) - r * FB; return m < FB ? m : FB; }
+  int64_t blk(int i, int k, int r, int c) const { return tile(i, k) + (int64_t)r * FB + (int64_t)c * FB * rows(i); }
+  void structure(int k, std::vector<int>& out) const {
+    out.clear();
+    if (k >= nt) return;
+    for (int i = k + 1; i <= k + nsub(k); ++i) out.push_back(i);
+    if (a > 0) out.push_back(nt);
+  }
+};
+
+// Build the task table of one plan kind, ordered by a list schedule on
+// `workers` persistent workers. Returns 0 or a negative stiles status code.
+int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out);
+
+// Consistency check of a task table: every wait names an existing counter
+// that enough tasks signal, and every such producer precedes the waiter in
+// claim order (the condition under which claim-order execution cannot
+// deadlock). Returns 0 or STILES_ERR_PLAN.
+int check_plan(const Plan& p);
+
+}  // namespace stiles
+#endif

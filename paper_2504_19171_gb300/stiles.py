@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in ``include/stiles.h`` (argument marshalling
+only: every step of the factorization and the selected inversion runs in the
+CUDA library).
+
+The low-level functions carry the C names (``stiles_create``,
+``stiles_factor`` ...) and take raw pointers; :class:`Stiles` wraps a handle
+with torch-allocated device buffers. The library is loaded from the in-tree
+build (``_build/libstiles.so``); importing this module raises if it is
+missing, and the launch functions raise if no CUDA device is present: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libstiles.so")
+
+STILES_OK = 0
+STILES_ERR_INVALID_ARG = -1
+STILES_ERR_NOT_SPD = -2
+STILES_ERR_TIMEOUT = -3
+STILES_ERR_CUDA = -4
+STILES_ERR_OOM = -5
+STILES_ERR_UNSUPPORTED = -6
+STILES_ERR_PLAN = -7
+STILES_FP64 = 0
+STILES_OPT_WAIT_BUDGET_NS = 1
+STILES_OPT_GRID = 2
+
+PLAN_FACTOR, PLAN_SELINV, PLAN_FUSED = 0, 1, 2
+
+EXPORTS = [
+    "stiles_create", "stiles_layout_doubles", "stiles_workspace_bytes", "stiles_factor", "stiles_selinv",
+    "stiles_factor_selinv", "stiles_logdet", "stiles_status", "stiles_set_option", "stiles_plan_stats",
+    "stiles_debug_check_corrupted", "stiles_debug_break_plan", "stiles_destroy", "stiles_strerror",
+]
+
+
+class StilesError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run paper_2504_19171_gb300.build.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "stiles_create": [i32, i32, i32, i32, i32, P(vp)],
+        "stiles_layout_doubles": [vp, P(sz)],
+        "stiles_workspace_bytes": [vp, P(sz), P(sz), P(sz)],
+        "stiles_factor": [vp, vp, vp, vp, vp],
+        "stiles_selinv": [vp, vp, vp, vp, vp],
+        "stiles_factor_selinv": [vp, vp, vp, vp, vp, vp],
+        "stiles_logdet": [vp, P(ctypes.c_double)],
+        "stiles_status": [vp, P(i32), P(i64), P(i64)],
+        "stiles_set_option": [vp, i32, i64],
+        "stiles_plan_stats": [i32, i32, i32, i32, i32, i32, P(i64)],
+        "stiles_debug_check_corrupted": [i32, i32, i32, i32, i32, i32],
+        "stiles_debug_break_plan": [vp, i32],
+        "stiles_destroy": [vp],
+        "stiles_strerror": [i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "stiles_strerror" else i32
+    return lib
+
+
+_lib = _load()
+
+
+def strerror(code: int) -> str:
+    return _lib.stiles_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != STILES_OK:
+        raise StilesError(rc, what)
+
+
+# ----------------------------------------------------------- C names -----
+def stiles_create(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.stiles_create(nt, b, band, arrow, precision, ctypes.byref(h)), "stiles_create")
+    return h.value
+
+
+def stiles_layout_doubles(h: int) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.stiles_layout_doubles(h, ctypes.byref(n)), "stiles_layout_doubles")
+    return n.value
+
+
+def stiles_workspace_bytes(h: int) -> Tuple[int, int, int]:
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.stiles_workspace_bytes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "stiles_workspace_bytes")
+    return a.value, b.value, c.value
+
+
+def stiles_factor(h: int, A_ptr: int, L_ptr: int, scratch_ptr: int, stream: int = 0) -> None:
+    _check(_lib.stiles_factor(h, A_ptr, L_ptr, scratch_ptr, stream), "stiles_factor")
+
+
+def stiles_selinv(h: int, L_ptr: int, S_ptr: int, scratch_ptr: int, stream: int = 0) -> None:
+    _check(_lib.stiles_selinv(h, L_ptr, S_ptr, scratch_ptr, stream), "stiles_selinv")
+
+
+def stiles_factor_selinv(h: int, A_ptr: int, L_ptr: int, S_ptr: int, scratch_ptr: int, stream: int = 0) -> None:
+    _check(_lib.stiles_factor_selinv(h, A_ptr, L_ptr, S_ptr, scratch_ptr, stream), "stiles_factor_selinv")
+
+
+def stiles_logdet(h: int) -> Tuple[int, float]:
+    """(status code, logdet); logdet is NaN unless the code is STILES_OK."""
+    v = ctypes.c_double(float("nan"))
+    rc = _lib.stiles_logdet(h, ctypes.byref(v))
+    return rc, (v.value if rc == STILES_OK else float("nan"))
+
+
+def stiles_status(h: int) -> Tuple[int, int, int]:
+    code, info, done = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.stiles_status(h, ctypes.byref(code), ctypes.byref(info), ctypes.byref(done)), "stiles_status")
+    return code.value, info.value, done.value
+
+
+def stiles_set_option(h: int, option: int, value: int) -> None:
+    _check(_lib.stiles_set_option(h, option, int(value)), "stiles_set_option")
+
+
+def stiles_plan_stats(nt: int, b: int, band: int, arrow: int, which: int, workers: int = 152) -> Dict[str, int]:
+    st = (ctypes.c_longlong * 8)()
+    _check(_lib.stiles_plan_stats(nt, b, band, arrow, which, workers, st), "stiles_plan_stats")
+    keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns"]
+    return dict(zip(keys, list(st)))
+
+
+def stiles_debug_check_corrupted(nt: int, b: int, band: int, arrow: int, which: int, mode: int) -> int:
+    return _lib.stiles_debug_check_corrupted(nt, b, band, arrow, which, mode)
+
+
+def stiles_debug_break_plan(h: int, which: int) -> None:
+    _check(_lib.stiles_debug_break_plan(h, which), "stiles_debug_break_plan")
+
+
+def stiles_destroy(h: Optional[int]) -> None:
+    _check(_lib.stiles_destroy(h), "stiles_destroy")
+
+
+# --------------------------------------------------------- layout -----
+class PackedLayout:
+    """Offsets of the packed band+arrow layout (column-major tiles; see the
+    header for the definition)."""
+
+    def __init__(self, nt: int, b: int, w: int, a: int):
+        self.nt, self.b, self.w, self.a = nt, b, min(w, nt - 1), a
+        self.colstride = (1 + self.w) * b * b + a * b
+        self.doubles = nt * self.colstride + a * a
+
+    def rows(self, i: int) -> int:
+        return self.a if i == self.nt else self.b
+
+    def offset(self, i: int, k: int) -> int:
+        if k == self.nt:
+            return self.nt * self.colstride
+        if i == self.nt:
+            return k * self.colstride + (1 + self.w) * self.b * self.b
+        return k * self.colstride + (i - k) * self.b * self.b
+
+    def pattern(self):
+        for k in range(self.nt):
+            yield (k, k)
+            for i in range(k + 1, min(k + self.w, self.nt - 1) + 1):
+                yield (i, k)
+            if self.a > 0:
+                yield (self.nt, k)
+        if self.a > 0:
+            yield (self.nt, self.nt)
+
+    def pack(self, tiles, out: np.ndarray) -> np.ndarray:
+        """Write a {(i,k): array} tile dict into the flat float64 array."""
+        for (i, k) in self.pattern():
+            r, c = self.rows(i), self.rows(k)
+            off = self.offset(i, k)
+            out[off:off + r * c] = np.asarray(tiles[(i, k)], dtype=np.float64).reshape(r, c).ravel(order="F")
+        return out
+
+    def unpack(self, flat: np.ndarray) -> Dict[Tuple[int, int], np.ndarray]:
+        res = {}
+        for (i, k) in self.pattern():
+            r, c = self.rows(i), self.rows(k)
+            off = self.offset(i, k)
+            res[(i, k)] = flat[off:off + r * c].reshape(c, r).T.copy()
+        return res
+
+    def tile_view(self, flat, i: int, k: int):
+        """(rows x cols) view of one tile of a flat array/tensor (transposed
+        strides: column-major storage)."""
+        r, c = self.rows(i), self.rows(k)
+        off = self.offset(i, k)
+        return flat[off:off + r * c].reshape(c, r).T
+
+
+# ------------------------------------------------------ torch helper -----
+class Stiles:
+    """One handle plus its device buffers (torch float64 tensors on CUDA)."""
+
+    def __init__(self, nt: int, b: int, band: int, arrow: int, device: str = "cuda", wait_budget_s: float = None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("stiles needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.h = stiles_create(nt, b, band, arrow, STILES_FP64)
+        self.layout = PackedLayout(nt, b, band, arrow)
+        self.nt, self.b, self.w, self.a = nt, b, self.layout.w, arrow
+        Lb, Sb, Wb = stiles_workspace_bytes(self.h)
+        self.doubles = Lb // 8
+        self.L = torch.empty(self.doubles, dtype=torch.float64, device=self.device)
+        self.S = torch.empty(self.doubles, dtype=torch.float64, device=self.device)
+        self.scratch = torch.empty(Wb, dtype=torch.uint8, device=self.device)
+        self.A = None
+        if wait_budget_s is not None:
+            stiles_set_option(self.h, STILES_OPT_WAIT_BUDGET_NS, int(wait_budget_s * 1e9))
+
+    def upload(self, M) -> "Stiles":
+        """Pack an ArrowheadTiles (host) into a device A buffer."""
+        host = self.layout.pack(M.tiles, np.zeros(self.doubles))
+        self.A = self.torch.from_numpy(host).to(self.device)
+        return self
+
+    def stream_ptr(self, stream=None) -> int:
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return int(s.cuda_stream)
+
+    def factor(self, stream=None, inplace: bool = False) -> None:
+        dst = self.A if inplace else self.L
+        if inplace:
+            self.L = self.A
+        stiles_factor(self.h, self.A.data_ptr(), dst.data_ptr(), self.scratch.data_ptr(), self.stream_ptr(stream))
+
+    def selinv(self, stream=None) -> None:
+        stiles_selinv(self.h, self.L.data_ptr(), self.S.data_ptr(), self.scratch.data_ptr(), self.stream_ptr(stream))
+
+    def factor_selinv(self, stream=None) -> None:
+        stiles_factor_selinv(self.h, self.A.data_ptr(), self.L.data_ptr(), self.S.data_ptr(),
+                             self.scratch.data_ptr(), self.stream_ptr(stream))
+
+    def status(self) -> Tuple[int, int, int]:
+        return stiles_status(self.h)
+
+    def logdet(self) -> float:
+        rc, v = stiles_logdet(self.h)
+        _check(rc, "stiles_logdet")
+        return v
+
+    def sigma_tiles(self) -> Dict[Tuple[int, int], np.ndarray]:
+        return self.layout.unpack(self.S.cpu().numpy())
+
+    def L_tiles(self) -> Dict[Tuple[int, int], np.ndarray]:
+        return self.layout.unpack(self.L.cpu().numpy())
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            stiles_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,82 @@
+"""Failure detection on the GPU without faulting it: non-SPD input reported
+LAPACK-style, a dependency that never arrives ends the launch with a TIMEOUT
+status after a short wait budget (the GPU stays usable), bad arguments are
+rejected before any launch."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_19171_gb300 import workloads as W
+from tests.gpu_helpers import FP64_TOL, need_gpu, rel_err, run_gpu
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tile,local", [(0, 0), (2, 5), (3, 70), (6, 3)])
+def test_not_spd_reports_first_failing_column(tile, local):
+    S = need_gpu()
+    M = W.random_arrowhead(6, 100, 1, 9, seed=3)
+    M.tiles[(tile, tile)][local, local] = -5.0
+    col = tile * M.b + local
+    with pytest.raises(O.OracleNotSPD) as e:
+        O.cholesky(M)
+    assert e.value.info == col + 1
+    for mode in ("fused", "split"):
+        _, _, _, status = run_gpu(M, mode)
+        assert status[0] == S.STILES_ERR_NOT_SPD
+        assert status[1] == col + 1
+
+
+@pytest.mark.gpu
+def test_nan_input_is_not_spd():
+    S = need_gpu()
+    M = W.random_arrowhead(4, 64, 1, 8, seed=1)
+    M.tiles[(1, 1)][3, 3] = np.nan
+    _, _, _, status = run_gpu(M, "fused")
+    assert status[0] == S.STILES_ERR_NOT_SPD and status[1] == 64 + 3 + 1
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("which", [0, 2])
+def test_stuck_dependency_times_out_and_gpu_recovers(which):
+    S = need_gpu()
+    import torch
+    M = W.random_arrowhead(6, 64, 1, 8, seed=2)
+    st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=0.5).upload(M)
+    try:
+        S.stiles_debug_break_plan(st.h, which)
+        st.factor() if which == 0 else st.factor_selinv()
+        code, info, done = st.status()
+        assert code == S.STILES_ERR_TIMEOUT
+        assert S.stiles_logdet(st.h)[0] == S.STILES_ERR_TIMEOUT
+    finally:
+        st.close()
+    torch.cuda.synchronize()
+    # the device is still healthy: a fresh handle computes the right answer
+    Lr, Sr, ldr = O.selinv(M)
+    L, Sg, ld, status = run_gpu(M, "fused")
+    assert status[0] == 0 and rel_err(Sg, Sr) < FP64_TOL
+
+
+@pytest.mark.gpu
+def test_bad_arguments_are_rejected():
+    S = need_gpu()
+    import torch
+    st = S.Stiles(3, 8, 1, 2)
+    try:
+        with pytest.raises(S.StilesError) as e:
+            S.stiles_factor(st.h, 0, st.L.data_ptr(), st.scratch.data_ptr(), 0)
+        assert e.value.code == S.STILES_ERR_INVALID_ARG
+        with pytest.raises(S.StilesError):
+            S.stiles_selinv(st.h, st.L.data_ptr(), st.L.data_ptr(), st.scratch.data_ptr(), 0)
+        with pytest.raises(S.StilesError):
+            S.stiles_selinv(st.h, st.L.data_ptr(), st.S.data_ptr(), st.scratch.data_ptr() + 8, 0)
+        with pytest.raises(S.StilesError):
+            S.stiles_set_option(st.h, S.STILES_OPT_WAIT_BUDGET_NS, 0)
+    finally:
+        st.close()
+    with pytest.raises(S.StilesError) as e:
+        S.stiles_create(0, 8, 1, 2)
+    assert e.value.code == S.STILES_ERR_INVALID_ARG
+    with pytest.raises(S.StilesError) as e:
+        S.stiles_create(3, 8, 1, 2, precision=7)
+    assert e.value.code == S.STILES_ERR_UNSUPPORTED

@@ -1,0 +1,87 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle,
+element by element on the same seeded inputs, for shapes that span several
+fine blocks per tile, ragged tile and arrow edges, and the degenerate cases
+(one tile column, no arrow, no band, scalar tiles)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_19171_gb300 import workloads as W
+from tests.gpu_helpers import FP64_TOL, need_gpu, rel_err, run_gpu
+
+SHAPES = [
+    (16, 64, 1, 16),   # the n = 1040 configuration
+    (5, 100, 2, 37),   # ragged tiles (64 + 36) and arrow (37)
+    (9, 130, 1, 70),   # three row blocks per tile (64 + 64 + 2), arrow 64 + 6
+    (4, 3, 1, 2),      # tiles smaller than one fine block
+    (1, 50, 0, 5),     # a single band tile column
+    (6, 64, 0, 0),     # block diagonal, no arrow
+    (7, 40, 4, 0),     # wide band, no arrow
+    (3, 200, 2, 1),    # arrow of width 1
+    (12, 64, 3, 64),
+    (30, 1, 1, 0),     # scalar tridiagonal
+    (10, 2, 3, 1),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("mode", ["fused", "split"])
+def test_parity_against_oracle(shape, mode):
+    M = W.random_arrowhead(*shape, seed=sum(shape))
+    Lr, Sr, ldr = O.selinv(M)
+    L, S, ld, status = run_gpu(M, mode)
+    assert status[0] == 0
+    assert rel_err(L, Lr) < FP64_TOL
+    assert rel_err(S, Sr) < FP64_TOL
+    assert abs(ld - ldr) < FP64_TOL * max(1.0, abs(ldr))
+    for i in range(M.nt + (1 if M.a else 0)):
+        T = S[(i, i)]
+        assert np.array_equal(T, T.T)
+        assert np.all(np.triu(L[(i, i)], 1) == 0)
+
+
+@pytest.mark.gpu
+def test_inplace_factor():
+    M = W.random_arrowhead(8, 96, 2, 20, seed=4)
+    Lr, Sr, ldr = O.selinv(M)
+    L, S, ld, status = run_gpu(M, "inplace")
+    assert status[0] == 0
+    assert rel_err(L, Lr) < FP64_TOL and rel_err(S, Sr) < FP64_TOL
+
+
+@pytest.mark.gpu
+def test_spatiotemporal_small_against_oracle():
+    M = W.spatiotemporal(nt=12, side=8, a=16, rho=0.9, tau=1.0, seed=0)  # b = 64
+    Lr, Sr, ldr = O.selinv(M)
+    L, S, ld, status = run_gpu(M, "fused")
+    assert status[0] == 0
+    assert rel_err(S, Sr) < FP64_TOL
+    assert abs(ld - ldr) < FP64_TOL * abs(ldr)
+
+
+@pytest.mark.gpu
+def test_kron_closed_form_band4():
+    side, nt, rho = 8, 10, 0.6
+    M = W.spatiotemporal(nt=nt, side=side, a=0, rho=rho, tau=0.0, band_power=4)
+    L, S, ld, status = run_gpu(M, "fused")
+    assert status[0] == 0
+    Qs_inv = np.linalg.inv(W.laplacian2d_plus_identity(side))
+    R = np.array([[rho ** abs(s - t) / (1 - rho * rho) for t in range(nt)] for s in range(nt)])
+    R4 = np.linalg.matrix_power(R, 4)
+    ref = {(i, k): R4[i, k] * Qs_inv for (i, k) in S}
+    kappa = np.linalg.cond(M.to_dense())
+    assert rel_err(S, ref) < max(1e-12, 50 * kappa * np.finfo(float).eps)
+
+
+@pytest.mark.gpu
+def test_bitwise_repeatable():
+    """Every block is reduced in a fixed order, so the dynamic claim order
+    does not change a single bit."""
+    M = W.random_arrowhead(10, 128, 2, 33, seed=8)
+    _, S1, ld1, _ = run_gpu(M, "fused")
+    _, S2, ld2, _ = run_gpu(M, "fused")
+    _, S3, ld3, _ = run_gpu(M, "split")
+    for key in S1:
+        assert np.array_equal(S1[key], S2[key]) and np.array_equal(S1[key], S3[key])
+    assert ld1 == ld2 == ld3
