@@ -1,0 +1,293 @@
+#!/usr/bin/env python3
+"""Benchmark: factorization + selected inversion of the spatio-temporal SPD
+block-arrowhead matrix (nt = 200 tiles of 1024, bandwidth 1 tile, arrow 64,
+n = 204,864; A = kron(Q_t, Q_s) + tau I plus a dense arrow) in FP64 on GB300.
+
+One step = one pass of the whole hot path: tiled Cholesky + phase 1 + phase 2
+(one persistent launch of stiles_factor_selinv) over the device-resident
+matrix. Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); each rank factors and inverts its
+own copy (independent matrices: replicas, no collective on the data path);
+value = all ranks' work / the slowest rank's time ("weak" scaling).
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload (the first two tile columns of the same matrix family plus the arrow).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "spatiotemporal_arrowhead_fp64", "nt": 200, "b": 1024, "w": 1, "a": 64, "n": 204864,
+            "Q_t": "AR(1) precision, rho=0.9", "Q_s": "2-D 5-point Laplacian + I on a 32x32 grid", "tau": 1.0,
+            "arrow": "64 columns N(0,1), corner diagonally dominant", "seed": 0}
+SAMPLE_NT = 2  # oracle sample: first 2 tile columns (n = 2*1024 + 64)
+METRIC = "factor+selinv TFLOP/s (FP64)"
+
+# FP64 FMA pipe of GB300: 2 DFMA per clock per SM (measured: 1.97/clk/SM with
+# >= 4 warps per SM), 152 SMs, 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+
+# DRAM traffic of the persistent kernel per launch from one ncu capture of a
+# smaller case of the same shape family, scaled to nt = 200 tile columns
+# (traffic grows linearly with nt). Valid only for the kernel source it was
+# measured on (sha256 prefix of stiles_kernel.cu + plan.cpp); else null.
+TRAFFIC = {"sources_sha": None, "bytes_per_launch": None}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("stiles_kernel.cu", "plan.cpp"):
+        with open(os.path.join(ROOT, "paper_2504_19171_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return self
+        self.proc = subprocess.Popen([exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                                      "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(nt_sample: int):
+    """Run the CPU oracle on the first nt_sample tile columns of the workload
+    family; returns (seconds, flops)."""
+    from oracle import oracle as O
+    from paper_2504_19171_gb300 import stiles as S
+    from paper_2504_19171_gb300 import workloads as W
+    M = W.spatiotemporal(nt=nt_sample, side=32, a=WORKLOAD["a"], rho=0.9, tau=WORKLOAD["tau"], seed=WORKLOAD["seed"])
+    flops = S.stiles_plan_stats(nt_sample, WORKLOAD["b"], WORKLOAD["w"], WORKLOAD["a"], S.PLAN_FUSED, 1)["flops"]
+    t0 = time.perf_counter()
+    O.selinv(M)
+    return time.perf_counter() - t0, flops
+
+
+def run_reference(args, world, rank):
+    """CPU oracle arm: rank 0 only; each step = the oracle on the bounded sample."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(1)  # warm-up: load and page in the oracle (CPU; nothing to warm on a device)
+    times, flops = [], 0
+    for _ in range(args.steps):
+        dt, flops = oracle_sample(SAMPLE_NT)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * flops / total / 1e12
+    sample = (f"CPU FP64 oracle (C, scalar, single thread) on the first {SAMPLE_NT} tile columns of the same "
+              f"matrix family plus the arrow (n = {SAMPLE_NT * 1024 + 64}, {flops / 1e9:.2f} GFLOP per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, sample_nt=SAMPLE_NT),
+            "matrices_per_s": args.steps / total * SAMPLE_NT / WORKLOAD["nt"],
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2504_19171_gb300 import build as B
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    from paper_2504_19171_gb300 import stiles as S
+    from paper_2504_19171_gb300 import workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    nt, b, w, a = args.nt, WORKLOAD["b"], WORKLOAD["w"], WORKLOAD["a"]
+    M = W.spatiotemporal(nt=nt, side=32, a=a, rho=0.9, tau=WORKLOAD["tau"], seed=WORKLOAD["seed"])
+    st = S.Stiles(nt, b, w, a, device=str(dev))
+    A_host = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).pin_memory()
+    del M
+    st.A = A_host.to(dev)
+    flops = S.stiles_plan_stats(nt, b, w, a, S.PLAN_FUSED, 152)["flops"]
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        st.factor_selinv(stream)
+    torch.cuda.synchronize(dev)
+    code, info, done = st.status()
+    if code != S.STILES_OK:
+        raise SystemExit(f"warm-up launch failed: {S.strerror(code)} info={info}")
+    logdet = st.logdet()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # device-resident timed region
+    barrier()
+    clocks = ClockSampler(dev.index if dev.index is not None else 0).start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev0 = starts[0]
+    ev0.record(stream)
+    for k in range(args.steps):
+        st.factor_selinv(stream)
+        starts[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    per_launch = [starts[k].elapsed_time(starts[k + 1]) / 1e3 for k in range(args.steps)]
+    t_local = ev0.elapsed_time(starts[-1]) / 1e3
+    code, info, _ = st.status()
+    if code != S.STILES_OK:
+        raise SystemExit(f"timed launch failed: {S.strerror(code)}")
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = world * args.steps * flops / t_max / 1e12
+
+    # end to end through the public API with host buffers (H2D of A, D2H of Sigma)
+    S_host = torch.empty(st.doubles if not args.no_e2e else 1, dtype=torch.float64).pin_memory()
+    e2e_value = None
+    if not args.no_e2e:
+        e2e_steps = args.steps
+        st.factor_selinv_host(A_host, S_host, stream)  # one untimed pass to settle the copy path
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            st.factor_selinv_host(A_host, S_host, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        te = torch.tensor([e0.elapsed_time(e1) / 1e3], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e_value = world * e2e_steps * flops / float(te.item()) / 1e12
+
+    achieved = flops / (sum(per_launch) / len(per_launch)) / 1e12
+    sha = kernel_sources_sha()
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha"] == sha else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, nt=nt, n=nt * b + a, parallelism=f"replicas{world}" if world > 1 else "single",
+                       flops_per_step=flops, flop_convention="tile ops: POTRF/TRTRI/LAUUM m^3/3, TRSM/TRMM m k^2, "
+                       "SYRK and symmetric Sigma_ii update m^2 k, GEMM 2mnk",
+                       l2="inputs larger than L2 (A, L, Sigma 3.45 GB each; L2 129 MB)"),
+        "matrices_per_s": world * args.steps / t_max,
+        "logdet": logdet,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_host.numel() * 8),
+                "d2h_bytes_per_step": int(S_host.numel() * 8 + 8)},
+        "gpu_launches": args.steps * (2 if not args.no_e2e else 1),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "stiles::persistent_kernel (FP64 pipe)",
+                     "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 pipe; tcgen05 has no f64 kind)"},
+    }
+    st.close()
+    if args.nt != WORKLOAD["nt"]:
+        line["config"]["workload"] += f"_nt{args.nt}_profiling_case"
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        dt, f = oracle_sample(SAMPLE_NT)
+        line["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {SAMPLE_NT} tile columns + arrow of the same matrix family "
+                                          f"(n = {SAMPLE_NT * 1024 + 64}, {f / 1e9:.2f} GFLOP) in {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],
+                    help="tile columns (default 200; smaller values are profiling cases, not bench lines)")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

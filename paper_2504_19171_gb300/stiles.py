@@ -256,6 +256,20 @@ class Stiles:
         stiles_factor_selinv(self.h, self.A.data_ptr(), self.L.data_ptr(), self.S.data_ptr(),
                              self.scratch.data_ptr(), self.stream_ptr(stream))
 
+    def factor_selinv_host(self, A_host, S_host, stream=None) -> float:
+        """End-to-end call with host buffers: copy the packed A (pinned host
+        float64 tensor) to the device, factor and invert in one launch, copy
+        Sigma back into S_host (pinned) and return logdet (synchronizes)."""
+        torch = self.torch
+        if self.A is None:
+            self.A = torch.empty(self.doubles, dtype=torch.float64, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.stream(s):
+            self.A.copy_(A_host, non_blocking=True)
+            self.factor_selinv(stream=s)
+            S_host.copy_(self.S, non_blocking=True)
+        return self.logdet()
+
     def status(self) -> Tuple[int, int, int]:
         return stiles_status(self.h)
 
