@@ -93,8 +93,9 @@ int stiles_layout_doubles(stiles_t h, size_t *doubles);
 
 /* Bytes the caller must provide: L and Sigma buffers (equal to the packed
  * size * 8) and a scratch buffer (device, 256-byte aligned) that holds
- * L_ii^{-1}, the scaled off-diagonal tiles L_ki L_ii^{-1} and the dependency
- * counters. Any pointer may be NULL to skip it. */
+ * L_ii^{-1}, the scaled off-diagonal tiles L_ki L_ii^{-1} and the device
+ * scheduler's state (dependency counters and ready queues). Any pointer may
+ * be NULL to skip it. */
 int stiles_workspace_bytes(stiles_t h, size_t *L_bytes, size_t *sigma_bytes, size_t *scratch_bytes);
 
 /* Tiled Cholesky (Sec. III): reads A_tiles (device, packed layout), writes
@@ -140,9 +141,20 @@ int stiles_status(stiles_t h, int *code, long long *info, long long *tasks_done)
 /* Options. STILES_OPT_WAIT_BUDGET_NS: bound of one device dependency wait in
  * nanoseconds (default 20 s); when it expires the launch stops with
  * STILES_ERR_TIMEOUT instead of hanging. STILES_OPT_GRID: persistent CTAs per
- * launch (0 = one per SM). */
-enum stiles_option { STILES_OPT_WAIT_BUDGET_NS = 1, STILES_OPT_GRID = 2 };
+ * launch (0 = the default, two per SM). STILES_OPT_TRACE: 1 allocates a
+ * device trace buffer (32 bytes per task) and makes every later launch record
+ * per-task %globaltimer stamps (read with stiles_trace); 0 frees it (default
+ * off: tracing costs one extra store per task). Returns STILES_ERR_INVALID_ARG
+ * for an unknown option or value. */
+enum stiles_option { STILES_OPT_WAIT_BUDGET_NS = 1, STILES_OPT_GRID = 2, STILES_OPT_TRACE = 3 };
 int stiles_set_option(stiles_t h, int option, long long value);
+
+/* Per-task trace of the last launch (tracing must be on). Waits for the
+ * launch. *n_tasks receives the task count of that launch; if out_host is not
+ * NULL it must hold capacity >= 4 * n_tasks words and receives, per task in
+ * claim order: claim time, dependencies-satisfied time, end time (ns of the
+ * GPU's global timer) and (sm id << 32 | cta << 8 | op). */
+int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size_t *n_tasks);
 
 /* Plan statistics for a shape, computed on the host (no GPU, no handle).
  * which: 0 = factor plan, 1 = selinv plan, 2 = fused plan; workers = number
@@ -165,8 +177,8 @@ int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers
  * STILES_ERR_PLAN). Host only. */
 int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode);
 
-/* Test hook: make the handle's plan `which` unsatisfiable on the device (the
- * last task waits for a counter that no task signals) without the host check,
+/* Test hook: make the handle's plan `which` unsatisfiable on the device (one
+ * task waits for one more predecessor than it has) without the host check,
  * so that a launch must end with STILES_ERR_TIMEOUT once the wait budget
  * expires. Used to test that a stuck dependency ends the kernel cleanly. */
 int stiles_debug_break_plan(stiles_t h, int which);

@@ -36,15 +36,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link the library. ``checked=True`` builds the self-checking
+    variant (``libstiles_checked.so``: every queue index and every task's
+    address range is validated on the device; a violation is reported as a
+    status instead of an access) used to diagnose device faults."""
     os.makedirs(BUILD, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "stiles.h")]
     common = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     jobs = []
     objs = []
+    suffix = "_checked" if checked else ""
+    lib = LIB if not checked else os.path.join(BUILD, "libstiles_checked.so")
+    if checked:
+        common = common + ["-DSTILES_CHECKED"]
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(BUILD, src + suffix + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc()] + common + ARCH + ["-lineinfo", "-c", s, "-o", o]
@@ -57,15 +65,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
             if res.returncode:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode:
             sys.stderr.write(res.stdout + res.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

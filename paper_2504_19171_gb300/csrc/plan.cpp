@@ -34,9 +34,10 @@
 namespace stiles {
 namespace {
 
-// Cost model for the list schedule (one worker = one SM of a GB300 at about
-// 1.9 GHz with 2 FP64 FMA per clock): ~7.6 flop/ns, plus a per-task overhead.
-constexpr double kFlopPerNs = 7.6;
+// Cost model for the list schedule: one SM of a GB300 at about 1.9 GHz with
+// 2 FP64 FMA per clock does ~7.6 flop/ns, shared by the kCtasPerSm workers
+// that run on it; plus a per-task overhead.
+constexpr double kFlopPerNs = 7.6 / kCtasPerSm;
 constexpr double kTaskOverheadNs = 2500.0;
 constexpr double kSweepStepNs = 120.0;  // one step of an in-shared-memory triangular sweep
 
@@ -69,9 +70,12 @@ struct Builder {
   int emit(Task t, std::vector<Seg> segs, std::vector<Wait> waits, std::vector<int32_t> sigs, double epi_ns) {
     double f = 0;
     for (const Seg& g : segs) f += 2.0 * t.m * t.n * g.k;
+    if (t.pmode == PM_TRI3) f *= 0.75;
     int id = (int)tasks.size();
     tasks.push_back(t);
-    cost.push_back(kTaskOverheadNs + f / kFlopPerNs + epi_ns);
+    // parts run side by side on different CTAs
+    cost.push_back(kTaskOverheadNs + f / kFlopPerNs / t.parts +
+                   epi_ns / (t.pmode == PM_ROWS2 ? 2 : t.pmode == PM_ROWS4 ? 4 : 1));
     tsegs.push_back(std::move(segs));
     twaits.push_back(std::move(waits));
     for (int32_t c : sigs) writers[c].push_back(id);
@@ -86,7 +90,19 @@ struct Builder {
     t.m = (int16_t)m;
     t.n = (int16_t)n;
     t.diag = -1;
+    t.parts = 1;
+    t.pmode = PM_FULL;
     return t;
+  }
+
+  // Divide a block task among CTAs; a mode that would leave a part empty
+  // (blocks of at most 32 rows or columns) falls back to one part.
+  static void split(Task& t, uint8_t mode) {
+    if (mode == PM_ROWS2 && t.m > 32) { t.pmode = PM_ROWS2; t.parts = 2; }
+    else if (mode == PM_ROWS4 && t.m > 48) { t.pmode = PM_ROWS4; t.parts = 4; }
+    else if (mode == PM_ROWS4 && t.m > 32) { t.pmode = PM_ROWS2; t.parts = 2; }
+    else if (mode == PM_QUAD4 && t.m > 32 && t.n > 32) { t.pmode = PM_QUAD4; t.parts = 4; }
+    else if (mode == PM_TRI3 && t.m > 32 && t.m == t.n) { t.pmode = PM_TRI3; t.parts = 3; }
   }
 
   static Seg seg(int64_t a, int lda, int64_t b, int ldb, int k, bool ta, bool tb) {
@@ -182,9 +198,18 @@ struct Builder {
     }
   }
 
+  // Global index of fine row block (i, r) (band tiles have nblk(0) blocks each).
+  int64_t grow(int i, int r) const { return (int64_t)i * L.nblk(0) + r; }
+
   void emit_block_chain(int i, int r, int kq, int cq) {
     const int m = L.bdim(i, r), n = L.bdim(kq, cq);
     const bool diag = (i == kq && r == cq);
+    // The factorization's critical path runs down the diagonal: POTRF of a
+    // diagonal block, the TRSM of the next two blocks below it, and the newest
+    // update of the next diagonal block and of the block below it. Those tasks
+    // are urgent: the device queues them ahead of all others.
+    const int64_t dist = grow(i, r) - grow(kq, cq);
+    const int64_t prev_col = grow(kq, cq) - 1;
     const int32_t me = lctr[lidx(i, kq, r, cq)];
     // terms: list of (source tile column k, first block c0, last block c1)
     struct Term { int k, c0, c1; };
@@ -214,7 +239,7 @@ struct Builder {
       w.push_back({lctr[lidx(i, t.k, r, t.c1)], lfinal[lidx(i, t.k, r, t.c1)]});
       w.push_back({lctr[lidx(kq, t.k, cq, t.c1)], lfinal[lidx(kq, t.k, cq, t.c1)]});
     };
-    size_t nfused = diag && !terms.empty() ? 1 : 0;  // POTRF absorbs its last update
+    const size_t nfused = 0;  // every update runs as its own (split) task
     size_t nchain = terms.size() - nfused;
     int total_writers = (int)nchain + 1;
     lfinal[lidx(i, kq, r, cq)] = total_writers;
@@ -224,6 +249,11 @@ struct Builder {
       tk.ldo = ld_i;
       tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
       tk.ldc = ld_i;
+      // a diagonal block only needs its lower quadrants; the newest update of
+      // a block gates its TRSM / POTRF on the critical path: split it 4 ways
+      if (diag) split(tk, PM_TRI3);
+      else if (t + 1 == nchain) split(tk, PM_QUAD4);
+      if (t + 1 == nchain && dist <= 1 && grow(terms[t].k, terms[t].c1) == prev_col) tk.flags |= TF_URGENT;
       std::vector<Wait> w;
       if (nwritten > 0) w.push_back({me, nwritten});
       term_waits(terms[t], w);
@@ -239,6 +269,8 @@ struct Builder {
       term_waits(terms[t], w);
     }
     Task tk = blank(diag ? OP_POTRF : OP_TRSM_RLT, m, n);
+    if (!diag) split(tk, PM_ROWS4);
+    if (dist <= 2) tk.flags |= TF_URGENT;
     tk.out = outref;
     tk.ldo = ld_i;
     tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
@@ -353,6 +385,7 @@ struct Builder {
       for (int c = 0; c <= r; ++c) {
         const int m = L.bdim(i, r), n = L.bdim(i, c);
         Task t = blank(OP_STORE, m, n);
+        if (r == c) split(t, PM_TRI3);  // only the lower part of a diagonal block is used
         t.out = mkref(BUF_S, L.blk(i, i, r, c));
         t.ldo = ld;
         std::vector<Wait> w{{linv_ctr(i, r), R - r}, {linv_ctr(i, c), R - c}};
@@ -391,6 +424,7 @@ struct Builder {
         for (int r = 0; r < L.nblk(j); ++r) {
           const int m = L.bdim(j, r), n = L.bdim(i, c);
           Task t = blank(OP_NEG, m, n);
+          split(t, PM_QUAD4);  // phase 2 is a chain of joins: shorter tasks, shorter steps
           t.out = mkref(BUF_S, L.blk(j, i, r, c));
           t.ldo = ldj;
           std::vector<Seg> segs;
@@ -422,6 +456,7 @@ struct Builder {
       for (int c = 0; c <= r; ++c) {
         const int m = L.bdim(i, r), n = L.bdim(i, c);
         Task t = blank(OP_SYMUPD, m, n);
+        split(t, r == c ? PM_TRI3 : PM_QUAD4);
         t.out = mkref(BUF_S, L.blk(i, i, r, c));
         t.ldo = ld;
         t.cin = t.out;
@@ -430,7 +465,7 @@ struct Builder {
           t.aux = mkref(BUF_S, L.blk(i, i, c, r));
           t.ldx = ld;
         } else {
-          t.flags = 1;
+          t.flags = TF_SYM_DIAG;
         }
         std::vector<Seg> segs;
         std::vector<Wait> w{{s0(i, r, c), 1}};
@@ -478,6 +513,8 @@ struct Builder {
       blevel[t] = cost[t] + best;
       cp = std::max(cp, blevel[t]);
     }
+    std::vector<double> tlevel(nt_, 0.0);
+    (void)tlevel;
     // list schedule: free workers take the ready task with the largest bottom level
     using RItem = std::pair<double, int32_t>;
     std::priority_queue<RItem> ready;
@@ -513,10 +550,12 @@ struct Builder {
       }
     }
     while (!running.empty()) { now = std::max(now, running.top().first); running.pop(); }
-    // write the plan in claim order
+    // write the plan in list-schedule order
     Plan& p = *out;
     p.tasks.clear(); p.segs.clear(); p.waits.clear(); p.sigs.clear();
     p.tasks.reserve(nt_);
+    std::vector<int32_t> rank(nt_);
+    for (int r = 0; r < nt_; ++r) rank[order[r]] = r;
     for (int32_t t : order) {
       Task tk = tasks[t];
       tk.seg0 = (int32_t)p.segs.size();
@@ -530,6 +569,40 @@ struct Builder {
       for (int32_t c : tsigs[t]) p.sigs.push_back(c);
       p.tasks.push_back(tk);
     }
+    // successor graph in schedule-order indices
+    p.indeg.assign(nt_, 0);
+    p.succ_off.assign(nt_ + 1, 0);
+    p.succ.clear();
+    for (int r = 0; r < nt_; ++r) {
+      const int32_t t = order[r];
+      p.succ_off[r] = (int32_t)p.succ.size();
+      for (int32_t q : succ[t]) {
+        p.succ.push_back(rank[q]);
+        p.indeg[rank[q]]++;
+      }
+    }
+    p.succ_off[nt_] = (int32_t)p.succ.size();
+    p.nbuckets = (nt_ + kTasksPerBucket - 1) / kTasksPerBucket;
+    p.slots0.assign((size_t)p.nbuckets * kSlotsPerBucket, -1);
+    p.tail0.assign(p.nbuckets, 0);
+    p.bcap.assign(p.nbuckets, 0);
+    p.urgent_parts = 0;
+    p.urgent_tail0 = 0;
+    for (int r = 0; r < nt_; ++r) {
+      const int parts = p.tasks[r].parts;
+      if (p.tasks[r].flags & TF_URGENT) {
+        p.urgent_parts += parts;
+        continue;
+      }
+      const int b = r / kTasksPerBucket;
+      p.bcap[b] += parts;
+      if (p.indeg[r] == 0)
+        for (int q = 0; q < parts; ++q) p.slots0[(size_t)b * kSlotsPerBucket + p.tail0[b]++] = 4 * r + q;
+    }
+    p.uslots0.assign(std::max(1, p.urgent_parts), -1);
+    for (int r = 0; r < nt_; ++r)
+      if ((p.tasks[r].flags & TF_URGENT) && p.indeg[r] == 0)
+        for (int q = 0; q < p.tasks[r].parts; ++q) p.uslots0[p.urgent_tail0++] = 4 * r + q;
     p.nctr = (int32_t)chain.size();
     p.ndiag = ndiag;
     p.flops = flops;
@@ -601,6 +674,7 @@ int check_plan(const Plan& p) {
     if (tk.seg0 < 0 || tk.nseg < 0 || (int64_t)tk.seg0 + tk.nseg > (int64_t)p.segs.size()) return STILES_ERR_PLAN;
     if (tk.sig0 < 0 || tk.nsig < 0 || (int64_t)tk.sig0 + tk.nsig > (int64_t)p.sigs.size()) return STILES_ERR_PLAN;
     if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_SYMUPD) return STILES_ERR_PLAN;
+    if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_ROWS4) return STILES_ERR_PLAN;
     for (int q = 0; q < tk.nwait; ++q) {
       const Wait& w = p.waits[tk.wait0 + q];
       if (w.ctr < 0 || w.ctr >= p.nctr) return STILES_ERR_PLAN;
@@ -612,6 +686,106 @@ int check_plan(const Plan& p) {
       seen[c]++;
     }
   }
+  return 0;
+}
+
+}  // namespace stiles
+
+namespace stiles {
+
+// Host emulation of one launch, for tests: every access of every task part
+// stays inside its buffer (A, L, Sigma, scratch tiles: `doubles` each), every
+// queue slot index stays inside its bucket or the urgent queue, and the
+// successor graph releases every task exactly once. Returns 0 or
+// STILES_ERR_PLAN (and prints the first problem to stderr).
+int validate_plan(const Plan& p, const Shape& s, int kind) {
+  // buffers a launch of this kind provides: factor A, L, scratch; selinv L, Sigma, scratch
+  const unsigned allowed = kind == PLAN_FACTOR ? 0xBu : kind == PLAN_SELINV ? 0xEu : 0xFu;
+  const Layout L(s);
+  const int64_t lim = L.doubles();
+  const int nt = (int)p.tasks.size();
+  auto bad = [&](const char* what, int t) {
+    fprintf(stderr, "validate_plan: %s (task %d, op %d)\n", what, t, t >= 0 ? (int)p.tasks[t].op : -1);
+    return STILES_ERR_PLAN;
+  };
+  auto in = [&](int64_t ref, int64_t lo_off, int64_t hi_off) {  // [ref+lo, ref+hi] inside its buffer
+    if (ref < 0) return false;
+    const int64_t off = ref & OFF_MASK;
+    const int buf = (int)(ref >> BUF_SHIFT);
+    return buf >= 0 && buf < 4 && ((allowed >> buf) & 1) && off + lo_off >= 0 && off + hi_off < lim;
+  };
+  for (int t = 0; t < nt; ++t) {
+    const Task& tk = p.tasks[t];
+    for (int q = 0; q < tk.parts; ++q) {
+      int r0 = 0, c0 = 0, rm = tk.m, cn = tk.n;
+      switch (tk.pmode) {
+        case PM_ROWS2: r0 = 32 * q; rm = std::min(32, tk.m - r0); break;
+        case PM_ROWS4: r0 = 16 * q; rm = std::min(16, tk.m - r0); break;
+        case PM_QUAD4: r0 = 32 * (q & 1); c0 = 32 * (q >> 1); break;
+        case PM_TRI3: r0 = q == 0 ? 0 : 32; c0 = q == 2 ? 32 : 0; break;
+        default: break;
+      }
+      if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3) { rm = std::min(32, tk.m - r0); cn = std::min(32, tk.n - c0); }
+      if (rm <= 0 || cn <= 0) continue;
+      const int r1 = r0 + rm - 1, c1 = c0 + cn - 1;
+      for (int g = tk.seg0; g < tk.seg0 + tk.nseg; ++g) {
+        const Seg& sg = p.segs[g];
+        if (sg.k <= 0) return bad("empty segment", t);
+        const int64_t amax = (sg.trans & 1) ? (sg.k - 1) + (int64_t)r1 * sg.lda : r1 + (int64_t)(sg.k - 1) * sg.lda;
+        const int64_t amin = (sg.trans & 1) ? (int64_t)r0 * sg.lda : r0;
+        const int64_t bmax = (sg.trans & 2) ? c1 + (int64_t)(sg.k - 1) * sg.ldb : (sg.k - 1) + (int64_t)c1 * sg.ldb;
+        const int64_t bmin = (sg.trans & 2) ? c0 : (int64_t)c0 * sg.ldb;
+        if (!in(sg.a, amin, amax)) return bad("segment A out of bounds", t);
+        if (!in(sg.b, bmin, bmax)) return bad("segment B out of bounds", t);
+      }
+      if (!in(tk.out, r0 + (int64_t)c0 * tk.ldo, r1 + (int64_t)c1 * tk.ldo)) return bad("output out of bounds", t);
+      const bool uses_cin = tk.op == OP_UPD || tk.op == OP_POTRF || tk.op == OP_TRSM_RLT || tk.op == OP_SYMUPD;
+      if (uses_cin && !in(tk.cin, r0 + (int64_t)c0 * tk.ldc, r1 + (int64_t)c1 * tk.ldc)) return bad("input out of bounds", t);
+      if (tk.op == OP_TRSM_RLT && !in(tk.aux, 0, (tk.n - 1) + (int64_t)(tk.n - 1) * tk.ldx)) return bad("T out of bounds", t);
+      if ((tk.op == OP_TRSM_LLN || tk.op == OP_TRTRI) && !in(tk.aux, 0, (tk.m - 1) + (int64_t)(tk.m - 1) * tk.ldx))
+        return bad("T out of bounds", t);
+      if (tk.op == OP_SYMUPD && !(tk.flags & TF_SYM_DIAG) &&
+          !in(tk.aux, c0 + (int64_t)r0 * tk.ldx, c1 + (int64_t)r1 * tk.ldx))
+        return bad("mirror out of bounds", t);
+      if (tk.op == OP_POTRF && tk.zrows > 0 && !in(tk.out, -(int64_t)tk.zrows, -1 + (int64_t)(tk.n - 1) * tk.ldo))
+        return bad("zeroed rows out of bounds", t);
+      if (tk.op == OP_POTRF && (tk.diag < 0 || tk.diag >= p.ndiag)) return bad("logdet slot out of range", t);
+    }
+  }
+  // queue emulation: pushes per bucket / urgent queue never exceed capacity
+  std::vector<int> rem(p.indeg), tail(p.tail0), seen(nt, 0);
+  int utail = p.urgent_tail0;
+  std::vector<int> stack;
+  for (int t = 0; t < nt; ++t)
+    if (p.indeg[t] == 0) stack.push_back(t);
+  int done = 0;
+  while (!stack.empty()) {
+    const int t = stack.back();
+    stack.pop_back();
+    if (seen[t]++) return bad("task released twice", t);
+    ++done;
+    for (int e = p.succ_off[t]; e < p.succ_off[t + 1]; ++e) {
+      const int sc = p.succ[e];
+      if (sc < 0 || sc >= nt) return bad("successor out of range", t);
+      if (--rem[sc] == 0) {
+        const int parts = p.tasks[sc].parts;
+        if (p.tasks[sc].flags & TF_URGENT) {
+          utail += parts;
+          if (utail > p.urgent_parts) return bad("urgent queue overflow", sc);
+        } else {
+          const int b = sc / kTasksPerBucket;
+          tail[b] += parts;
+          if (tail[b] > p.bcap[b] || tail[b] > kSlotsPerBucket) return bad("bucket overflow", sc);
+        }
+        stack.push_back(sc);
+      }
+      if (rem[sc] < 0) return bad("predecessor count underflow", sc);
+    }
+  }
+  if (done != nt) return bad("some tasks never become ready", -1);
+  for (int b = 0; b < p.nbuckets; ++b)
+    if (tail[b] != p.bcap[b]) return bad("bucket not filled exactly", b * kTasksPerBucket);
+  if (utail != p.urgent_parts) return bad("urgent queue not filled exactly", -1);
   return 0;
 }
 

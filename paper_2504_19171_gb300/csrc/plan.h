@@ -19,6 +19,7 @@
 namespace stiles {
 
 constexpr int FB = 64;  // fine block order (rows and columns of one task's output)
+constexpr int kCtasPerSm = 2;  // persistent CTAs (workers) per SM
 
 // Buffer ids, stored in the top bits of a 64-bit element offset.
 enum Buf : int { BUF_A = 0, BUF_L = 1, BUF_S = 2, BUF_W = 3 };
@@ -35,6 +36,22 @@ enum Op : uint8_t {
   OP_STORE = 5,     // out = acc
   OP_NEG = 6,       // out = -acc
   OP_SYMUPD = 7,    // out = cin - acc and its transpose into the mirror block (aux)
+};
+
+// How a task's output block is divided among CTAs (each part runs as its own
+// queue entry; the last part to finish releases the task's successors).
+enum PartMode : uint8_t {
+  PM_FULL = 0,   // one part: the whole block
+  PM_ROWS2 = 1,  // rows [0,32) and [32,64)
+  PM_QUAD4 = 2,  // the four 32 x 32 quadrants
+  PM_TRI3 = 3,   // quadrants (0,0), (1,0), (1,1): a diagonal block's lower part
+  PM_ROWS4 = 4,  // rows [0,16), [16,32), [32,48), [48,64)
+};
+
+// Task flags.
+enum TaskFlag : uint8_t {
+  TF_SYM_DIAG = 1,  // OP_SYMUPD on a diagonal block (mirror inside the block)
+  TF_URGENT = 2,    // on the critical path: queued ahead of the buckets
 };
 
 struct Seg {       // acc += op(A) (m x k) * op(B) (k x n)
@@ -60,10 +77,12 @@ struct Task {        // 64 bytes
   int32_t sig0;      // signals: sig[sig0 .. sig0+nsig)
   int16_t nsig;
   uint8_t op;
-  uint8_t flags;     // bit 0: SYMUPD on a diagonal block (mirror inside the block)
+  uint8_t flags;     // TaskFlag bits
   int32_t diag;      // POTRF: index of its logdet partial sum
   int32_t zrows;     // POTRF: rows above the block in its tile column to zero (L's strict upper part)
   int32_t gcol;      // POTRF: 0-based global column of the block's first pivot
+  uint8_t parts;     // 1..4 queue entries (see PartMode)
+  uint8_t pmode;
 };
 static_assert(sizeof(Task) == 80, "task layout");
 
@@ -80,11 +99,29 @@ struct Shape {
   int nt, b, w, a;  // w already clipped to nt-1
 };
 
+// Dynamic schedule: a task becomes ready when its last predecessor finishes
+// (device counter rem[t], initialised to indeg[t]) and is pushed into the
+// bucket of its expected start time in the list schedule; workers pop from the
+// earliest non-empty bucket. Buckets hold kTasksPerBucket consecutive tasks of
+// the list-schedule order.
+constexpr int kTasksPerBucket = 64;
+constexpr int kSlotsPerBucket = 4 * kTasksPerBucket;  // up to 4 parts per task
+
 struct Plan {
-  std::vector<Task> tasks;  // in claim order
+  std::vector<Task> tasks;  // in list-schedule order
   std::vector<Seg> segs;
-  std::vector<Wait> waits;
+  std::vector<Wait> waits;  // counter form of the dependencies (host checks)
   std::vector<int32_t> sigs;
+  std::vector<int32_t> indeg;     // predecessors per task
+  std::vector<int32_t> succ_off;  // successors: succ[succ_off[t] .. succ_off[t+1])
+  std::vector<int32_t> succ;
+  std::vector<int32_t> slots0;    // initial bucket slots: ready tasks at the front, -1 elsewhere
+  std::vector<int32_t> tail0;     // initial ready parts per bucket
+  std::vector<int32_t> bcap;      // parts per bucket (a bucket is finished when all were popped)
+  std::vector<int32_t> uslots0;   // initial urgent queue (ready urgent parts first, -1 elsewhere)
+  int32_t urgent_parts = 0;       // capacity of the urgent queue
+  int32_t urgent_tail0 = 0;
+  int32_t nbuckets = 0;
   int32_t nctr = 0;         // dependency counters used
   int32_t ndiag = 0;        // logdet partial sums (one per POTRF task)
   double flops = 0;         // algorithmic flops (tile-operation convention)
@@ -128,6 +165,10 @@ int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out);
 // claim order (the condition under which claim-order execution cannot
 // deadlock). Returns 0 or STILES_ERR_PLAN.
 int check_plan(const Plan& p);
+
+// Host emulation of a launch of the plan (bounds of every access, queue
+// capacities, every task released once). Returns 0 or STILES_ERR_PLAN.
+int validate_plan(const Plan& p, const Shape& s, int kind);
 
 }  // namespace stiles
 #endif

@@ -14,17 +14,39 @@
 #include "stiles_device.h"
 
 using namespace stiles;
+using stiles::sched_state_at;
 
 namespace {
 
 struct DevPlan {
   Task* tasks = nullptr;
   Seg* segs = nullptr;
-  Wait* waits = nullptr;
-  int32_t* sigs = nullptr;
+  int32_t* succ_off = nullptr;
+  int32_t* succ = nullptr;
+  int32_t* bcap = nullptr;
+  int32_t* image = nullptr;  // initial scheduler state (copied to scratch before each launch)
+  size_t image_ints = 0;
   int ntasks = 0;
-  int nctr = 0;
+  int nbuckets = 0;
+  int ucap = 0;
 };
+
+// Initial scheduler state of a plan: rem = indeg, slots = slots0, tail = tail0,
+// head = 0, gcnt = ready tasks per group of 32 buckets, lo = 0.
+std::vector<int32_t> sched_image(const Plan& p) {
+  const int nt = (int)p.tasks.size(), nb = p.nbuckets;
+  std::vector<int32_t> img(sched_state_ints(nt, nb, p.urgent_parts), 0);
+  SchedState q = sched_state_at(img.data(), nt, nb, p.urgent_parts);
+  for (int t = 0; t < nt; ++t) q.rem[t] = p.indeg[t];
+  for (size_t i = 0; i < p.slots0.size(); ++i) q.slots[i] = p.slots0[i];
+  for (int b = 0; b < nb; ++b) {
+    q.tail[b] = p.tail0[b];
+    q.gcnt[b >> 5] += p.tail0[b];
+  }
+  for (size_t i = 0; i < p.uslots0.size(); ++i) q.uslots[i] = p.uslots0[i];
+  q.lo[8] = p.urgent_tail0;
+  return img;
+}
 
 template <typename T>
 int upload(const std::vector<T>& v, T** out) {
@@ -48,10 +70,12 @@ struct stiles_handle {
   DevStatus* dstatus = nullptr;  // one block per plan kind
   double* dlogdet = nullptr;
   int ndiag = 0;
-  int nctr_max = 0;
+  size_t state_ints_max = 0;
   size_t w_bytes = 0;        // scratch: L^{-1} and U tiles (packed layout)
-  size_t ctr_offset = 0;     // scratch: counters start (bytes)
+  size_t ctr_offset = 0;     // scratch: scheduler state start (bytes)
   size_t scratch_bytes = 0;
+  unsigned long long* dtrace = nullptr;  // optional per-task trace (STILES_OPT_TRACE)
+  size_t trace_tasks = 0;
   cudaStream_t last_stream = nullptr;
   bool launched = false;
   int last_kind = -1;         // plan kind of the last launch
@@ -65,11 +89,14 @@ static void free_handle(stiles_handle* h) {
   for (auto& d : h->dev) {
     cudaFree(d.tasks);
     cudaFree(d.segs);
-    cudaFree(d.waits);
-    cudaFree(d.sigs);
+    cudaFree(d.succ_off);
+    cudaFree(d.succ);
+    cudaFree(d.bcap);
+    cudaFree(d.image);
   }
   cudaFree(h->dstatus);
   cudaFree(h->dlogdet);
+  cudaFree(h->dtrace);
   delete h;
 }
 
@@ -86,7 +113,7 @@ extern "C" int stiles_create(int nt, int b, int band, int arrow, int precision, 
     delete h;
     return STILES_ERR_CUDA;
   }
-  h->grid = h->sms;
+  h->grid = h->sms * kCtasPerSm;
   for (int k = 0; k < 3; ++k) {
     int rc = build_plan(h->s, (PlanKind)k, h->grid, &h->plans[k]);
     if (rc) {
@@ -99,11 +126,16 @@ extern "C" int stiles_create(int nt, int b, int band, int arrow, int precision, 
     Plan& p = h->plans[k];
     rc = upload(p.tasks, &h->dev[k].tasks);
     if (!rc) rc = upload(p.segs, &h->dev[k].segs);
-    if (!rc) rc = upload(p.waits, &h->dev[k].waits);
-    if (!rc) rc = upload(p.sigs, &h->dev[k].sigs);
+    if (!rc) rc = upload(p.succ_off, &h->dev[k].succ_off);
+    if (!rc) rc = upload(p.succ, &h->dev[k].succ);
+    if (!rc) rc = upload(p.bcap, &h->dev[k].bcap);
+    std::vector<int32_t> img = sched_image(p);
+    if (!rc) rc = upload(img, &h->dev[k].image);
+    h->dev[k].image_ints = img.size();
     h->dev[k].ntasks = (int)p.tasks.size();
-    h->dev[k].nctr = p.nctr;
-    if (p.nctr > h->nctr_max) h->nctr_max = p.nctr;
+    h->dev[k].nbuckets = p.nbuckets;
+    h->dev[k].ucap = p.urgent_parts;
+    if (img.size() > h->state_ints_max) h->state_ints_max = img.size();
     if (p.ndiag > h->ndiag) h->ndiag = p.ndiag;
   }
   if (!rc && cudaMalloc((void**)&h->dstatus, 3 * sizeof(DevStatus)) != cudaSuccess) rc = STILES_ERR_OOM;
@@ -116,7 +148,7 @@ extern "C" int stiles_create(int nt, int b, int band, int arrow, int precision, 
   Layout L(h->s);
   h->w_bytes = align_up((size_t)L.doubles() * sizeof(double), 256);
   h->ctr_offset = h->w_bytes;
-  h->scratch_bytes = align_up(h->ctr_offset + sizeof(int) * ((size_t)h->nctr_max + 1), 256);
+  h->scratch_bytes = align_up(h->ctr_offset + sizeof(int) * h->state_ints_max, 256);
   *out = h;
   return STILES_OK;
 }
@@ -143,21 +175,23 @@ static int launch(stiles_t h, int kind, const double* A, double* L, double* S, v
   cudaStream_t st = (cudaStream_t)stream;
   const DevPlan& d = h->dev[kind];
   char* scr = (char*)scratch;
-  int* ctr = (int*)(scr + h->ctr_offset);
-  int* claim = ctr + h->nctr_max;
-  if (cudaMemsetAsync(ctr, 0, sizeof(int) * ((size_t)d.nctr), st) != cudaSuccess) return STILES_ERR_CUDA;
-  if (cudaMemsetAsync(claim, 0, sizeof(int), st) != cudaSuccess) return STILES_ERR_CUDA;
+  int* state = (int*)(scr + h->ctr_offset);
+  if (d.image_ints &&
+      cudaMemcpyAsync(state, d.image, sizeof(int) * d.image_ints, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return STILES_ERR_CUDA;
   DevStatus* ds = h->dstatus + kind;
   if (cudaMemsetAsync(ds, 0, sizeof(DevStatus), st) != cudaSuccess) return STILES_ERR_CUDA;
   if (cudaMemsetAsync(&ds->spd_col, 0xff, sizeof(unsigned long long), st) != cudaSuccess) return STILES_ERR_CUDA;
   KParams p{};
   p.tasks = d.tasks;
   p.segs = d.segs;
-  p.waits = d.waits;
-  p.sigs = d.sigs;
+  p.succ_off = d.succ_off;
+  p.succ = d.succ;
+  p.bcap = d.bcap;
   p.ntasks = d.ntasks;
-  p.ctr = ctr;
-  p.claim = claim;
+  p.nbuckets = d.nbuckets;
+  p.ucap = d.ucap;
+  p.q = sched_state_at(state, d.ntasks, d.nbuckets, d.ucap);
   p.st = ds;
   p.logdet_part = h->dlogdet;
   p.buf[BUF_A] = const_cast<double*>(A);
@@ -165,6 +199,8 @@ static int launch(stiles_t h, int kind, const double* A, double* L, double* S, v
   p.buf[BUF_S] = S;
   p.buf[BUF_W] = (double*)scr;
   p.budget_ns = h->budget_ns;
+  p.trace = h->dtrace;
+  p.buf_len = Layout(h->s).doubles();
   h->last_stream = st;
   h->launched = true;
   h->last_kind = kind;
@@ -200,6 +236,7 @@ static int read_status(stiles_t h, int kind, DevStatus* ds) {
 static int code_of(const DevStatus& ds) {
   if (ds.code == STILES_DEV_NOT_SPD) return STILES_ERR_NOT_SPD;
   if (ds.code == STILES_DEV_TIMEOUT) return STILES_ERR_TIMEOUT;
+  if (ds.code == STILES_DEV_CHECK) return STILES_ERR_PLAN;
   return STILES_OK;
 }
 
@@ -216,7 +253,7 @@ extern "C" int stiles_status(stiles_t h, int* code, long long* info, long long* 
   if (rc) return rc;
   const int c = code_of(ds);
   if (code) *code = c;
-  if (info) *info = c == STILES_ERR_NOT_SPD ? (long long)ds.spd_col + 1 : c == STILES_ERR_TIMEOUT ? (long long)ds.info : 0;
+  if (info) *info = c == STILES_ERR_NOT_SPD ? (long long)ds.spd_col + 1 : c != STILES_OK ? (long long)ds.info : 0;
   if (tasks_done) *tasks_done = (long long)ds.done;
   return STILES_OK;
 }
@@ -248,8 +285,24 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
       return STILES_OK;
     case STILES_OPT_GRID:
       if (value < 0 || value > 65535) return STILES_ERR_INVALID_ARG;
-      h->grid = value == 0 ? h->sms : (int)value;
+      h->grid = value == 0 ? h->sms * kCtasPerSm : (int)value;
       return STILES_OK;
+    case STILES_OPT_TRACE: {
+      if (value != 0 && value != 1) return STILES_ERR_INVALID_ARG;
+      if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
+      if (h->launched && cudaStreamSynchronize(h->last_stream) != cudaSuccess) return STILES_ERR_CUDA;
+      cudaFree(h->dtrace);
+      h->dtrace = nullptr;
+      h->trace_tasks = 0;
+      if (value) {
+        size_t n = 0;
+        for (auto& d : h->dev) n = (size_t)d.ntasks > n ? (size_t)d.ntasks : n;
+        if (cudaMalloc((void**)&h->dtrace, 4 * sizeof(unsigned long long) * (n ? n : 1)) != cudaSuccess)
+          return STILES_ERR_OOM;
+        h->trace_tasks = n;
+      }
+      return STILES_OK;
+    }
     default:
       return STILES_ERR_INVALID_ARG;
   }
@@ -299,19 +352,31 @@ extern "C" int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, 
 extern "C" int stiles_debug_break_plan(stiles_t h, int which) {
   if (!h || which < 0 || which > 2) return STILES_ERR_INVALID_ARG;
   Plan& p = h->plans[which];
-  if (p.tasks.empty() || p.waits.empty()) return STILES_ERR_INVALID_ARG;
-  // the first task with a wait now needs a signal count no task provides
+  // the first task with a predecessor now waits for one more that never comes
   for (size_t t = 0; t < p.tasks.size(); ++t)
-    if (p.tasks[t].nwait > 0) {
-      Wait w = p.waits[p.tasks[t].wait0];
-      w.need = 1 << 30;
+    if (p.indeg[t] > 0) {
+      const int32_t v = p.indeg[t] + 1;
       if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
-      if (cudaMemcpy(h->dev[which].waits + p.tasks[t].wait0, &w, sizeof(Wait), cudaMemcpyHostToDevice) != cudaSuccess)
+      if (cudaMemcpy(h->dev[which].image + t, &v, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
         return STILES_ERR_CUDA;
-      p.waits[p.tasks[t].wait0] = w;
+      p.indeg[t] = v;
       return STILES_OK;
     }
   return STILES_ERR_INVALID_ARG;
+}
+
+extern "C" int stiles_trace(stiles_t h, unsigned long long* out_host, size_t capacity, size_t* n_tasks) {
+  if (!h || !n_tasks) return STILES_ERR_INVALID_ARG;
+  if (!h->dtrace || !h->launched) return STILES_ERR_INVALID_ARG;
+  const size_t n = (size_t)h->dev[h->last_kind].ntasks;
+  *n_tasks = n;
+  if (!out_host) return STILES_OK;
+  if (capacity < 4 * n) return STILES_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return STILES_ERR_CUDA;
+  if (n && cudaMemcpy(out_host, h->dtrace, 4 * sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return STILES_ERR_CUDA;
+  return STILES_OK;
 }
 
 extern "C" int stiles_destroy(stiles_t h) {

@@ -9,7 +9,7 @@
 namespace stiles {
 
 // Device status codes (the host maps them to stiles_status_code).
-enum : int { STILES_DEV_OK = 0, STILES_DEV_NOT_SPD = 1, STILES_DEV_TIMEOUT = 2 };
+enum : int { STILES_DEV_OK = 0, STILES_DEV_NOT_SPD = 1, STILES_DEV_TIMEOUT = 2, STILES_DEV_CHECK = 3 };
 
 struct DevStatus {
   int code;                    // first error (STILES_DEV_*)
@@ -19,18 +19,63 @@ struct DevStatus {
   unsigned long long spd_col;  // NOT_SPD: smallest failing global column (0-based); ~0 if none
 };
 
+// Per-launch scheduler state, one contiguous int32 block in the caller's
+// scratch, reset before every launch from a device image built at create:
+//   rem[ntasks]      predecessors not yet finished (image: indeg)
+//   pdone[ntasks]    parts of the task finished so far
+//   slots[nb*kSlotsPerBucket]  bucket b owns slots [b*kSlotsPerBucket, +kSlotsPerBucket)
+//   tail[nbuckets]   pushes into the bucket so far
+//   head[nbuckets]   pops from the bucket so far
+//   gcnt[ngroups]    ready tasks per group of 32 buckets (a scan hint)
+//   uslots[ucap]     urgent queue (critical-path tasks), popped before any bucket
+//   lo[32]           lo[0]: every bucket below it is finished (all popped);
+//                    lo[8]: urgent tail, lo[16]: urgent head
+struct SchedState {
+  int* rem;
+  int* pdone;
+  int* slots;
+  int* tail;
+  int* head;
+  int* gcnt;
+  int* uslots;
+  int* lo;
+};
+
+inline size_t sched_state_ints(int ntasks, int nbuckets, int ucap) {
+  const int ngroups = (nbuckets + 31) / 32;
+  return 2 * (size_t)ntasks + (size_t)nbuckets * kSlotsPerBucket + 2 * (size_t)nbuckets + (size_t)ngroups +
+         (size_t)(ucap > 0 ? ucap : 1) + 32;
+}
+
+inline SchedState sched_state_at(int* base, int ntasks, int nbuckets, int ucap) {
+  SchedState s;
+  s.rem = base;
+  s.pdone = s.rem + ntasks;
+  s.slots = s.pdone + ntasks;
+  s.tail = s.slots + (size_t)nbuckets * kSlotsPerBucket;
+  s.head = s.tail + nbuckets;
+  s.gcnt = s.head + nbuckets;
+  s.uslots = s.gcnt + (nbuckets + 31) / 32;
+  s.lo = s.uslots + (ucap > 0 ? ucap : 1);
+  return s;
+}
+
 struct KParams {
   const Task* tasks;
   const Seg* segs;
-  const Wait* waits;
-  const int32_t* sigs;
+  const int32_t* succ_off;  // successors in schedule order
+  const int32_t* succ;
+  const int32_t* bcap;  // parts per bucket
   int ntasks;
-  int* ctr;             // dependency counters (zeroed before the launch)
-  int* claim;           // next task to claim (zeroed before the launch)
+  int nbuckets;
+  int ucap;             // urgent queue capacity
+  SchedState q;         // mutable scheduler state
   DevStatus* st;        // status block (reset before the launch)
   double* logdet_part;  // one partial sum of log diag(L) per POTRF task
   double* buf[4];       // BUF_A, BUF_L, BUF_S, BUF_W base pointers
   long long budget_ns;  // bound of one dependency wait
+  unsigned long long* trace;  // optional: 4 words per task (claim, ready, end ns; sm/cta/op), or null
+  long long buf_len;          // doubles in each of buf[0..3] (self-checking builds)
 };
 
 size_t kernel_smem_bytes();

@@ -18,7 +18,9 @@ from typing import Dict, Optional, Tuple
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libstiles.so")
+# STILES_CHECKED=1 selects the self-checking build (diagnostics only)
+LIB_PATH = os.path.join(_PKG, "_build", "libstiles_checked.so" if os.environ.get("STILES_CHECKED") == "1"
+                        else "libstiles.so")
 
 STILES_OK = 0
 STILES_ERR_INVALID_ARG = -1
@@ -31,13 +33,14 @@ STILES_ERR_PLAN = -7
 STILES_FP64 = 0
 STILES_OPT_WAIT_BUDGET_NS = 1
 STILES_OPT_GRID = 2
+STILES_OPT_TRACE = 3
 
 PLAN_FACTOR, PLAN_SELINV, PLAN_FUSED = 0, 1, 2
 
 EXPORTS = [
     "stiles_create", "stiles_layout_doubles", "stiles_workspace_bytes", "stiles_factor", "stiles_selinv",
     "stiles_factor_selinv", "stiles_logdet", "stiles_status", "stiles_set_option", "stiles_plan_stats",
-    "stiles_debug_check_corrupted", "stiles_debug_break_plan", "stiles_destroy", "stiles_strerror",
+    "stiles_debug_check_corrupted", "stiles_debug_break_plan", "stiles_destroy", "stiles_strerror", "stiles_trace",
 ]
 
 
@@ -68,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "stiles_debug_break_plan": [vp, i32],
         "stiles_destroy": [vp],
         "stiles_strerror": [i32],
+        "stiles_trace": [vp, P(ctypes.c_ulonglong), sz, P(sz)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -149,6 +153,17 @@ def stiles_debug_check_corrupted(nt: int, b: int, band: int, arrow: int, which: 
 
 def stiles_debug_break_plan(h: int, which: int) -> None:
     _check(_lib.stiles_debug_break_plan(h, which), "stiles_debug_break_plan")
+
+
+def stiles_trace(h: int) -> np.ndarray:
+    """Per-task trace of the last launch as an (n, 4) uint64 array: claim,
+    ready and end times (ns) and (sm << 32 | cta << 8 | op)."""
+    n = ctypes.c_size_t()
+    _check(_lib.stiles_trace(h, None, 0, ctypes.byref(n)), "stiles_trace")
+    out = np.zeros((n.value, 4), dtype=np.uint64)
+    _check(_lib.stiles_trace(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), out.size, ctypes.byref(n)),
+           "stiles_trace")
+    return out
 
 
 def stiles_destroy(h: Optional[int]) -> None:

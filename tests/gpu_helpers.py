@@ -22,7 +22,7 @@ def rel_err(got: dict, ref: dict) -> float:
     return num / den if den > 0 else num
 
 
-def run_gpu(M, mode="fused", budget_s=None):
+def run_gpu(M, mode="fused", budget_s=5.0):
     """Factor and invert M on the GPU. Returns (L tiles, Sigma tiles,
     logdet, (code, info, done))."""
     S = need_gpu()

@@ -26,7 +26,7 @@ B = SIDE * SIDE
 def run_full(M):
     S = need_gpu()
     import torch
-    st = S.Stiles(M.nt, M.b, M.w, M.a).upload(M)
+    st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=10.0).upload(M)
     try:
         st.factor_selinv()
         torch.cuda.synchronize()
