@@ -71,7 +71,8 @@ enum stiles_status_code {
   STILES_ERR_CUDA = -4,        /* a CUDA runtime call failed */
   STILES_ERR_OOM = -5,         /* host or device allocation for the handle failed */
   STILES_ERR_UNSUPPORTED = -6, /* precision or option not available */
-  STILES_ERR_PLAN = -7         /* a task table failed its consistency check */
+  STILES_ERR_PLAN = -7,        /* a task table failed its consistency check */
+  STILES_ERR_TOO_LARGE = -8    /* the shape's scratch does not fit the fixed no-allocation array */
 };
 
 enum stiles_precision { STILES_FP64 = 0 };
@@ -120,6 +121,31 @@ int stiles_selinv(stiles_t h, const double *L_tiles, double *Sigma_tiles, void *
  * either). Asynchronous. */
 int stiles_factor_selinv(stiles_t h, const double *A_tiles, double *L_tiles, double *Sigma_tiles, void *scratch,
                          void *stream);
+
+/* Allocation-free variant of stiles_factor_selinv (the paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory when they run the factorization, such as services whose device
+ * memory is reserved once at start-up by their own allocator and may not grow
+ * while serving, or code that must not call cudaMalloc at that point).
+ * Same arguments as stiles_factor_selinv minus `scratch`: instead of a
+ * caller buffer it uses a fixed array of STILES_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) defined in the library (a file-scope __device__ array, so every
+ * GPU that loads the library holds it until the process exits). The call
+ * allocates nothing. The handle must already exist (stiles_create allocates
+ * its task tables when it is created, not here).
+ *   - Shapes whose scratch (stiles_workspace_bytes) exceeds the array return
+ *     STILES_ERR_TOO_LARGE and launch nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call, from every handle, shares the one array and leaves its
+ *     contents behind; each call re-initialises the part that must start from
+ *     a known state (the scheduler state) on its stream before the launch.
+ *     Calls whose launches overlap on the GPU (other streams, other threads)
+ *     race on the array: serialise them.
+ * Status and logdet are read as usual with stiles_status / stiles_logdet. */
+#define STILES_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int stiles_factor_selinv_noalloc(stiles_t h, const double *A_tiles, double *L_tiles, double *Sigma_tiles, void *stream);
 
 /* logdet(A) = 2 * sum log diag(L) from the last factorization of this handle
  * (stiles_factor or stiles_factor_selinv; a later stiles_selinv does not

@@ -6,6 +6,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -225,6 +226,40 @@ extern "C" int stiles_factor_selinv(stiles_t h, const double* A, double* L, doub
   return launch(h, PLAN_FUSED, A, L, S, scratch, stream);
 }
 
+// Scratch of stiles_factor_selinv_noalloc: one fixed array per device that
+// loads the library, shared by every call (see include/stiles.h).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STILES_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Device address of the array on `device` (which must be current). Looked up
+// once per device; the host-side name of the array is not a device address.
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return STILES_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return STILES_ERR_CUDA;
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return STILES_OK;
+}
+}  // namespace
+
+extern "C" int stiles_factor_selinv_noalloc(stiles_t h, const double* A, double* L, double* S, void* stream) {
+  if (!h || !A || !L || !S || S == L || (const double*)S == A) return STILES_ERR_INVALID_ARG;
+  if (h->scratch_bytes > STILES_NOALLOC_SCRATCH_BYTES) return STILES_ERR_TOO_LARGE;
+  if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
+  void* scratch = nullptr;
+  const int rc = noalloc_scratch(h->device, &scratch);
+  if (rc) return rc;
+  return launch(h, PLAN_FUSED, A, L, S, scratch, stream);
+}
+
 static int read_status(stiles_t h, int kind, DevStatus* ds) {
   if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
   if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return STILES_ERR_CUDA;
@@ -399,6 +434,7 @@ extern "C" const char* stiles_strerror(int code) {
     case STILES_ERR_OOM: return "out of memory";
     case STILES_ERR_UNSUPPORTED: return "unsupported option";
     case STILES_ERR_PLAN: return "task table failed its consistency check";
+    case STILES_ERR_TOO_LARGE: return "shape too large for the fixed no-allocation scratch";
     default: return "unknown status";
   }
 }

@@ -30,6 +30,8 @@ STILES_ERR_CUDA = -4
 STILES_ERR_OOM = -5
 STILES_ERR_UNSUPPORTED = -6
 STILES_ERR_PLAN = -7
+STILES_ERR_TOO_LARGE = -8
+NOALLOC_SCRATCH_BYTES = 64 << 20
 STILES_FP64 = 0
 STILES_OPT_WAIT_BUDGET_NS = 1
 STILES_OPT_GRID = 2
@@ -41,6 +43,7 @@ EXPORTS = [
     "stiles_create", "stiles_layout_doubles", "stiles_workspace_bytes", "stiles_factor", "stiles_selinv",
     "stiles_factor_selinv", "stiles_logdet", "stiles_status", "stiles_set_option", "stiles_plan_stats",
     "stiles_debug_check_corrupted", "stiles_debug_break_plan", "stiles_destroy", "stiles_strerror", "stiles_trace",
+    "stiles_factor_selinv_noalloc",
 ]
 
 
@@ -72,6 +75,7 @@ def _load() -> ctypes.CDLL:
         "stiles_destroy": [vp],
         "stiles_strerror": [i32],
         "stiles_trace": [vp, P(ctypes.c_ulonglong), sz, P(sz)],
+        "stiles_factor_selinv_noalloc": [vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -121,6 +125,14 @@ def stiles_selinv(h: int, L_ptr: int, S_ptr: int, scratch_ptr: int, stream: int 
 
 def stiles_factor_selinv(h: int, A_ptr: int, L_ptr: int, S_ptr: int, scratch_ptr: int, stream: int = 0) -> None:
     _check(_lib.stiles_factor_selinv(h, A_ptr, L_ptr, S_ptr, scratch_ptr, stream), "stiles_factor_selinv")
+
+
+def stiles_factor_selinv_noalloc(h: int, A_ptr: int, L_ptr: int, S_ptr: int, stream: int = 0) -> None:
+    """Factor + selected inversion without any device allocation: the scratch
+    is the library's fixed 64 MiB array (shared by all calls; see the C
+    header). Raises StilesError(STILES_ERR_TOO_LARGE) for shapes whose scratch
+    does not fit."""
+    _check(_lib.stiles_factor_selinv_noalloc(h, A_ptr, L_ptr, S_ptr, stream), "stiles_factor_selinv_noalloc")
 
 
 def stiles_logdet(h: int) -> Tuple[int, float]:
