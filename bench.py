@@ -41,11 +41,12 @@ METRIC = "factor+selinv TFLOP/s (FP64)"
 # >= 4 warps per SM), 152 SMs, 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
-# DRAM traffic of the persistent kernel per launch from one ncu capture of a
-# smaller case of the same shape family, scaled to nt = 200 tile columns
-# (traffic grows linearly with nt). Valid only for the kernel source it was
-# measured on (sha256 prefix of stiles_kernel.cu + plan.cpp); else null.
-TRAFFIC = {"sources_sha": None, "bytes_per_launch": None}
+# DRAM traffic of the persistent kernel per launch, from ncu captures of the
+# nt = 8 and nt = 16 cases of the same matrix family (0.862 GB and 2.309 GB):
+# the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
+# Valid only for the kernel source it was measured on (sha256 prefix of
+# stiles_kernel.cu + plan.cpp); otherwise reported as null.
+TRAFFIC = {"sources_sha": "206eb0fcd6b9f0ef", "bytes_per_launch": 35.59e9}
 
 
 def kernel_sources_sha() -> str:
