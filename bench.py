@@ -157,6 +157,44 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def measure_variants(S, st, stream, dev, flops, logdet64, args):
+    """The same step in the reduced-precision modes (emulated FP64 on bf16
+    tensor cores, FP32-class), on the FP64 handle's device-resident A. Error
+    is measured against this run's FP64 Sigma: max |Sigma_v - Sigma_64| /
+    max |Sigma_64| over every selected entry, and the relative logdet error.
+    TFLOP/s counts the same FP64-equivalent algorithmic flops."""
+    import torch
+    out = {}
+    S64 = st.S
+    smax = float(S64.abs().max().item())
+    for name, prec in (("emu64", S.STILES_EMU64), ("fp32x", S.STILES_FP32X)):
+        sv = S.Stiles(st.nt, st.b, st.w, st.a, device=str(dev), precision=prec)
+        sv.A = st.A
+        sv.factor_selinv(stream)
+        torch.cuda.synchronize(dev)
+        code = sv.status()[0]
+        if code != S.STILES_OK:
+            out[name] = {"status": S.strerror(code)}
+            sv.close()
+            continue
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.variant_steps + 1)]
+        ev[0].record(stream)
+        for k in range(args.variant_steps):
+            sv.factor_selinv(stream)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        t = ev[0].elapsed_time(ev[-1]) / 1e3 / args.variant_steps
+        ld = sv.logdet()
+        err = float((sv.S - S64).abs().max().item()) / smax
+        out[name] = {"value": flops / t / 1e12, "unit": "TFLOP/s (FP64-equivalent flops)", "ms_per_step": 1e3 * t,
+                     "steps": args.variant_steps, "speedup_vs_fp64": None,
+                     "sigma_err_vs_fp64": err, "logdet_rel_err_vs_fp64": abs(ld - logdet64) / abs(logdet64)}
+        sv.A = None
+        sv.close()
+        del sv
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -236,7 +274,13 @@ def run_ours(args, world, rank, local):
             torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
         e2e_value = world * e2e_steps * flops / float(te.item()) / 1e12
 
+    variants = None if args.no_variants else measure_variants(S, st, stream, dev, flops, logdet, args)
+
     achieved = flops / (sum(per_launch) / len(per_launch)) / 1e12
+    if variants:
+        for v in variants.values():
+            if "ms_per_step" in v:
+                v["speedup_vs_fp64"] = (1e3 * t_max / args.steps) / v["ms_per_step"]
     sha = kernel_sources_sha()
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha"] == sha else None
     line = {
@@ -253,6 +297,7 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_host.numel() * 8),
                 "d2h_bytes_per_step": int(S_host.numel() * 8 + 8)},
         "gpu_launches": args.steps * (2 if not args.no_e2e else 1),
+        "variants": variants,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "stiles::persistent_kernel (FP64 pipe)",
@@ -280,6 +325,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the EMU64 / FP32X lines")
+    ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],
                     help="tile columns (default 200; smaller values are profiling cases, not bench lines)")
     args = ap.parse_args()

@@ -44,7 +44,9 @@
  * (its status block and the caller's scratch are per launch).
  *
  * Precision. STILES_FP64 computes everything in IEEE binary64 on the FP64
- * pipe (GB300's tcgen05 tensor cores have no FP64 kind).
+ * pipe (GB300's tcgen05 tensor cores have no FP64 kind); STILES_EMU64 and
+ * STILES_FP32X lower only the off-diagonal bulk products (see
+ * stiles_precision).
  *
  * Errors. Every function returns STILES_OK (0) or a negative code. Launch
  * functions only report argument and CUDA launch errors; numerical status
@@ -75,12 +77,25 @@ enum stiles_status_code {
   STILES_ERR_TOO_LARGE = -8    /* the shape's scratch does not fit the fixed no-allocation array */
 };
 
-enum stiles_precision { STILES_FP64 = 0 };
+/* Precision of the off-diagonal bulk products (the factor's GEMM/SYRK
+ * updates, the TRMM of phase 1, and the products of phase 2). The diagonal
+ * POTRF, TRSM, TRTRI, LAUUM and the Sigma_ii assembly (subtract, mirror)
+ * always run in FP64.
+ *   STILES_FP64   IEEE binary64 on the FP64 pipe.
+ *   STILES_EMU64  emulated FP64: every operand is split, per row / column of
+ *                 its panel, into six signed 8-bit integer digits held
+ *                 exactly in bf16; digit products run on the tensor cores
+ *                 with exact FP32 accumulation per K chunk, move into int32
+ *                 level sums and are recombined in FP64 (split-precision
+ *                 scheme of Ozaki, Ogita, Oishi and Rump). Relative error of a
+ *                 product about 2^-47 of (max |row| x max |column|).
+ *   STILES_FP32X  FP32-class: operands rounded to FP32, FP32 FMA accumulation. */
+enum stiles_precision { STILES_FP64 = 0, STILES_EMU64 = 1, STILES_FP32X = 2 };
 
 /* Create a handle for one matrix shape.
  *   nt >= 1 band tile columns, b >= 1 tile order, band = w >= 0 lower tile
  *   bandwidth (clipped to nt-1), arrow = a >= 0 arrow width,
- *   precision = STILES_FP64.
+ *   precision = STILES_FP64, STILES_EMU64 or STILES_FP32X.
  * Builds the task DAG of the factorization, of the selected inversion and of
  * both fused (host, C++), orders each by a critical-path list schedule, and
  * uploads the tables. Returns STILES_ERR_INVALID_ARG for a bad shape,
@@ -121,6 +136,19 @@ int stiles_selinv(stiles_t h, const double *L_tiles, double *Sigma_tiles, void *
  * either). Asynchronous. */
 int stiles_factor_selinv(stiles_t h, const double *A_tiles, double *L_tiles, double *Sigma_tiles, void *scratch,
                          void *stream);
+
+/* End-to-end form of stiles_factor_selinv for callers whose matrix lives in
+ * host memory: on `stream`, copy A_host (stiles_layout_doubles doubles, the
+ * packed tile layout) into the device buffer A_dev, run the fused factor +
+ * selected inversion into L_dev / Sigma_dev, and copy Sigma_dev back into
+ * Sigma_host. Host buffers should be page-locked (cudaHostAlloc /
+ * torch pin_memory) for the copies to be asynchronous; they must stay valid
+ * until the stream reaches the end of the call. Device buffers follow the
+ * rules of stiles_factor_selinv (A_dev may alias L_dev). Asynchronous: read
+ * the status / logdet afterwards as usual. A_host and Sigma_host may be the
+ * same buffer (the input is consumed before Sigma is written back). */
+int stiles_factor_selinv_host(stiles_t h, const double *A_host, double *Sigma_host, double *A_dev, double *L_dev,
+                              double *Sigma_dev, void *scratch, void *stream);
 
 /* Allocation-free variant of stiles_factor_selinv (the paper has no
  * counterpart: this is an interface for callers that cannot allocate device
@@ -169,21 +197,24 @@ int stiles_status(stiles_t h, int *code, long long *info, long long *tasks_done)
  * STILES_ERR_TIMEOUT instead of hanging. STILES_OPT_GRID: persistent CTAs per
  * launch (0 = the default, two per SM). STILES_OPT_TRACE: 1 allocates a
  * device trace buffer (32 bytes per task) and makes every later launch record
- * per-task %globaltimer stamps (read with stiles_trace); 0 frees it (default
- * off: tracing costs one extra store per task). Returns STILES_ERR_INVALID_ARG
+ * per-part %globaltimer stamps (read with stiles_trace); 0 frees it (default
+ * off: tracing costs a few extra stores per part). Returns STILES_ERR_INVALID_ARG
  * for an unknown option or value. */
 enum stiles_option { STILES_OPT_WAIT_BUDGET_NS = 1, STILES_OPT_GRID = 2, STILES_OPT_TRACE = 3 };
 int stiles_set_option(stiles_t h, int option, long long value);
 
-/* Per-task trace of the last launch (tracing must be on). Waits for the
+/* Per-part trace of the last launch (tracing must be on). Waits for the
  * launch. *n_tasks receives the task count of that launch; if out_host is not
- * NULL it must hold capacity >= 4 * n_tasks words and receives, per task in
- * claim order: claim time, dependencies-satisfied time, end time (ns of the
- * GPU's global timer) and (sm id << 32 | cta << 8 | op). */
+ * NULL it must hold capacity >= 16 * n_tasks words and receives 4 records of
+ * 4 words per task (one per possible part, in list-schedule order; records of
+ * parts a task does not have are zero): time the worker started looking for
+ * work, time it got this part, end time (ns of the GPU's global timer), and
+ * (sm << 32 | cta << 12 | precision << 10 | last part << 9 | urgent << 8 | op). */
 int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size_t *n_tasks);
 
 /* Plan statistics for a shape, computed on the host (no GPU, no handle).
- * which: 0 = factor plan, 1 = selinv plan, 2 = fused plan; workers = number
+ * which: 0 = factor plan, 1 = selinv plan, 2 = fused plan, plus 16 x the
+ * stiles_precision of the plan (e.g. 2 + 16 * STILES_EMU64); workers = number
  * of persistent workers the list schedule assumes (e.g. the SM count).
  * stats[0] tasks, [1] segments, [2] waits, [3] counters,
  * [4] algorithmic flops of the tile operations (POTRF, TRTRI, LAUUM m^3/3;
@@ -195,6 +226,13 @@ int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size
  * Returns STILES_ERR_INVALID_ARG for a bad shape, STILES_ERR_PLAN if the
  * table fails its consistency check. */
 int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]);
+
+/* Test hook: build the plan `which` (as in stiles_plan_stats) for a shape and
+ * emulate one launch of it on the host: every memory access of every task
+ * part stays inside its buffer, every queue stays inside its capacity, and
+ * every task is released exactly once. Returns STILES_OK or STILES_ERR_PLAN
+ * (the first problem is printed to stderr). Host only. */
+int stiles_debug_validate(int nt, int b, int band, int arrow, int which);
 
 /* Test hook: build the plan `which` for a shape, corrupt its dependency table
  * on the host (mode 1: one wait names a counter beyond the table; mode 2: one

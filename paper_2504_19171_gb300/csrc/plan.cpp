@@ -71,6 +71,8 @@ struct Builder {
     double f = 0;
     for (const Seg& g : segs) f += 2.0 * t.m * t.n * g.k;
     if (t.pmode == PM_TRI3) f *= 0.75;
+    if (t.prec == PREC_EMU64) f /= 10.0;   // measured order of the emulated-FP64 speed-up per block
+    if (t.prec == PREC_FP32X) f /= 25.0;
     int id = (int)tasks.size();
     tasks.push_back(t);
     // parts run side by side on different CTAs
@@ -92,6 +94,7 @@ struct Builder {
     t.diag = -1;
     t.parts = 1;
     t.pmode = PM_FULL;
+    t.prec = PREC_FP64;
     return t;
   }
 
@@ -103,6 +106,19 @@ struct Builder {
     else if (mode == PM_ROWS4 && t.m > 32) { t.pmode = PM_ROWS2; t.parts = 2; }
     else if (mode == PM_QUAD4 && t.m > 32 && t.n > 32) { t.pmode = PM_QUAD4; t.parts = 4; }
     else if (mode == PM_TRI3 && t.m > 32 && t.m == t.n) { t.pmode = PM_TRI3; t.parts = 3; }
+  }
+
+  // Mark a bulk product task with the plan's reduced precision. The emulated
+  // FP64 kernel works on sub-tiles of at most 32 x 32: blocks that are not
+  // already split that way run as a grid of such tiles.
+  void lower_precision(Task& t) const {
+    if (s.prec == PREC_FP64) return;
+    t.prec = (uint8_t)s.prec;
+    if (s.prec == PREC_EMU64 && t.pmode != PM_QUAD4 && t.pmode != PM_TRI3) {
+      const int pr = t.m > 32 ? 2 : 1, pc = t.n > 32 ? 2 : 1;
+      t.pmode = PM_TILE32;
+      t.parts = (uint8_t)(pr * pc);
+    }
   }
 
   static Seg seg(int64_t a, int lda, int64_t b, int ldb, int k, bool ta, bool tb) {
@@ -204,12 +220,15 @@ struct Builder {
   void emit_block_chain(int i, int r, int kq, int cq) {
     const int m = L.bdim(i, r), n = L.bdim(kq, cq);
     const bool diag = (i == kq && r == cq);
-    // The factorization's critical path runs down the diagonal: POTRF of a
-    // diagonal block, the TRSM of the next two blocks below it, and the newest
-    // update of the next diagonal block and of the block below it. Those tasks
-    // are urgent: the device queues them ahead of all others.
+    // The factorization's critical path runs down the diagonal: POTRF(c) ->
+    // TRSM(c+1, c) -> update of (c+1, c+1) from column c -> POTRF(c+1). Tasks
+    // at the frontier are urgent (queued ahead of all others): every POTRF,
+    // the TRSMs of the kUrgentReach blocks below a diagonal block, and the
+    // updates from block column c into blocks whose row is within
+    // kUrgentReach of c. Work further below has slack of one block step or
+    // more and runs in list-schedule order, so the urgent queue stays short.
+    constexpr int64_t kUrgentReach = 3;
     const int64_t dist = grow(i, r) - grow(kq, cq);
-    const int64_t prev_col = grow(kq, cq) - 1;
     const int32_t me = lctr[lidx(i, kq, r, cq)];
     // terms: list of (source tile column k, first block c0, last block c1)
     struct Term { int k, c0, c1; };
@@ -253,7 +272,8 @@ struct Builder {
       // a block gates its TRSM / POTRF on the critical path: split it 4 ways
       if (diag) split(tk, PM_TRI3);
       else if (t + 1 == nchain) split(tk, PM_QUAD4);
-      if (t + 1 == nchain && dist <= 1 && grow(terms[t].k, terms[t].c1) == prev_col) tk.flags |= TF_URGENT;
+      if (grow(i, r) - grow(terms[t].k, terms[t].c1) <= kUrgentReach) tk.flags |= TF_URGENT;
+      lower_precision(tk);
       std::vector<Wait> w;
       if (nwritten > 0) w.push_back({me, nwritten});
       term_waits(terms[t], w);
@@ -270,7 +290,7 @@ struct Builder {
     }
     Task tk = blank(diag ? OP_POTRF : OP_TRSM_RLT, m, n);
     if (!diag) split(tk, PM_ROWS4);
-    if (dist <= 2) tk.flags |= TF_URGENT;
+    if (diag || dist <= kUrgentReach) tk.flags |= TF_URGENT;
     tk.out = outref;
     tk.ldo = ld_i;
     tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
@@ -408,6 +428,7 @@ struct Builder {
           w.push_back({linv_ctr(i, c), R - c});
           Seg g = seg(mkref(BUF_L, L.blk(k, i, r, c)), ldk, mkref(BUF_W, L.blk(i, i, c, c)), ld, ld - c * FB, false,
                       false);
+          lower_precision(t);
           emit(t, {g}, w, {ucol(k, i, c)}, 0.0);
         }
     }
@@ -447,6 +468,7 @@ struct Builder {
             }
             w.push_back({ucol(k, i, c), L.nblk(k)});
           }
+          lower_precision(t);
           emit(t, segs, w, {srow(j, i, r), scol(j, i, c)}, 0.0);
         }
       tile_gemms += (long long)st.size();
@@ -476,6 +498,7 @@ struct Builder {
           w.push_back({scol(k, i, r), L.nblk(k)});
           w.push_back({ucol(k, i, c), L.nblk(k)});
         }
+        if (!segs.empty()) lower_precision(t);  // the products; the assembly (cin - acc, mirror) stays FP64
         emit(t, segs, w, {srow(i, i, r), scol(i, i, c)}, 0.0);
       }
     tile_gemms += (long long)st.size();
@@ -550,7 +573,7 @@ struct Builder {
       }
     }
     while (!running.empty()) { now = std::max(now, running.top().first); running.pop(); }
-    // write the plan in list-schedule order
+    // write the plan in list-schedule order (the device queue order)
     Plan& p = *out;
     p.tasks.clear(); p.segs.clear(); p.waits.clear(); p.sigs.clear();
     p.tasks.reserve(nt_);
@@ -674,7 +697,7 @@ int check_plan(const Plan& p) {
     if (tk.seg0 < 0 || tk.nseg < 0 || (int64_t)tk.seg0 + tk.nseg > (int64_t)p.segs.size()) return STILES_ERR_PLAN;
     if (tk.sig0 < 0 || tk.nsig < 0 || (int64_t)tk.sig0 + tk.nsig > (int64_t)p.sigs.size()) return STILES_ERR_PLAN;
     if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_SYMUPD) return STILES_ERR_PLAN;
-    if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_ROWS4) return STILES_ERR_PLAN;
+    if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_TILE32 || tk.prec > PREC_FP32X) return STILES_ERR_PLAN;
     for (int q = 0; q < tk.nwait; ++q) {
       const Wait& w = p.waits[tk.wait0 + q];
       if (w.ctr < 0 || w.ctr >= p.nctr) return STILES_ERR_PLAN;
@@ -723,9 +746,19 @@ int validate_plan(const Plan& p, const Shape& s, int kind) {
         case PM_ROWS4: r0 = 16 * q; rm = std::min(16, tk.m - r0); break;
         case PM_QUAD4: r0 = 32 * (q & 1); c0 = 32 * (q >> 1); break;
         case PM_TRI3: r0 = q == 0 ? 0 : 32; c0 = q == 2 ? 32 : 0; break;
+        case PM_TILE32: {
+          const int pr = tk.m > 32 ? 2 : 1;
+          r0 = 32 * (q % pr); c0 = 32 * (q / pr);
+          break;
+        }
         default: break;
       }
-      if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3) { rm = std::min(32, tk.m - r0); cn = std::min(32, tk.n - c0); }
+      if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3 || tk.pmode == PM_TILE32) {
+        rm = std::min(32, tk.m - r0); cn = std::min(32, tk.n - c0);
+      }
+      if (tk.prec == PREC_EMU64 && (rm > 32 || cn > 32)) return bad("emulated task part larger than 32 x 32", t);
+      if (tk.prec != PREC_FP64 && tk.op != OP_UPD && tk.op != OP_NEG && tk.op != OP_STORE && tk.op != OP_SYMUPD)
+        return bad("reduced precision on a triangular task", t);
       if (rm <= 0 || cn <= 0) continue;
       const int r1 = r0 + rm - 1, c1 = c0 + cn - 1;
       for (int g = tk.seg0; g < tk.seg0 + tk.nseg; ++g) {

@@ -46,6 +46,14 @@ enum PartMode : uint8_t {
   PM_QUAD4 = 2,  // the four 32 x 32 quadrants
   PM_TRI3 = 3,   // quadrants (0,0), (1,0), (1,1): a diagonal block's lower part
   PM_ROWS4 = 4,  // rows [0,16), [16,32), [32,48), [48,64)
+  PM_TILE32 = 5, // a grid of at most 2 x 2 sub-tiles of at most 32 x 32 (parts = row tiles x column tiles)
+};
+
+// Arithmetic of a task's block products (its epilogue is always FP64).
+enum Precision : uint8_t {
+  PREC_FP64 = 0,   // FP64 FMA pipe
+  PREC_EMU64 = 1,  // split-precision emulated FP64: 6 bf16 digit planes per operand on the tensor cores
+  PREC_FP32X = 2,  // FP32 FMA pipe (FP32-class)
 };
 
 // Task flags.
@@ -83,6 +91,7 @@ struct Task {        // 64 bytes
   int32_t gcol;      // POTRF: 0-based global column of the block's first pivot
   uint8_t parts;     // 1..4 queue entries (see PartMode)
   uint8_t pmode;
+  uint8_t prec;      // Precision of the block products
 };
 static_assert(sizeof(Task) == 80, "task layout");
 
@@ -97,6 +106,7 @@ enum PlanKind : int { PLAN_FACTOR = 0, PLAN_SELINV = 1, PLAN_FUSED = 2 };
 
 struct Shape {
   int nt, b, w, a;  // w already clipped to nt-1
+  int prec = PREC_FP64;  // precision of the off-diagonal bulk products (Precision)
 };
 
 // Dynamic schedule: a task becomes ready when its last predecessor finishes

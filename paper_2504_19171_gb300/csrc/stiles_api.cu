@@ -42,10 +42,13 @@ std::vector<int32_t> sched_image(const Plan& p) {
   for (size_t i = 0; i < p.slots0.size(); ++i) q.slots[i] = p.slots0[i];
   for (int b = 0; b < nb; ++b) {
     q.tail[b] = p.tail0[b];
+    q.avail[b] = p.tail0[b];
     q.gcnt[b >> 5] += p.tail0[b];
+    q.scnt[b >> 10] += p.tail0[b];
   }
   for (size_t i = 0; i < p.uslots0.size(); ++i) q.uslots[i] = p.uslots0[i];
   q.lo[8] = p.urgent_tail0;
+  q.lo[24] = p.urgent_tail0;
   return img;
 }
 
@@ -105,10 +108,10 @@ extern "C" int stiles_create(int nt, int b, int band, int arrow, int precision, 
   if (!out) return STILES_ERR_INVALID_ARG;
   *out = nullptr;
   if (nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
-  if (precision != STILES_FP64) return STILES_ERR_UNSUPPORTED;
+  if (precision != STILES_FP64 && precision != STILES_EMU64 && precision != STILES_FP32X) return STILES_ERR_UNSUPPORTED;
   stiles_handle* h = new (std::nothrow) stiles_handle();
   if (!h) return STILES_ERR_OOM;
-  h->s = Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow};
+  h->s = Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision};
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;
@@ -201,6 +204,8 @@ static int launch(stiles_t h, int kind, const double* A, double* L, double* S, v
   p.buf[BUF_W] = (double*)scr;
   p.budget_ns = h->budget_ns;
   p.trace = h->dtrace;
+  if (h->dtrace && cudaMemsetAsync(h->dtrace, 0, 16 * sizeof(unsigned long long) * h->trace_tasks, st) != cudaSuccess)
+    return STILES_ERR_CUDA;
   p.buf_len = Layout(h->s).doubles();
   h->last_stream = st;
   h->launched = true;
@@ -224,6 +229,20 @@ extern "C" int stiles_selinv(stiles_t h, const double* L, double* S, void* scrat
 extern "C" int stiles_factor_selinv(stiles_t h, const double* A, double* L, double* S, void* scratch, void* stream) {
   if (!A || !L || !S || S == L || (const double*)S == A || (void*)S == scratch) return STILES_ERR_INVALID_ARG;
   return launch(h, PLAN_FUSED, A, L, S, scratch, stream);
+}
+
+extern "C" int stiles_factor_selinv_host(stiles_t h, const double* A_host, double* S_host, double* A_dev,
+                                         double* L_dev, double* S_dev, void* scratch, void* stream) {
+  if (!h || !A_host || !S_host || !A_dev || !L_dev || !S_dev || S_dev == L_dev || S_dev == A_dev ||
+      (void*)S_dev == scratch)
+    return STILES_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)Layout(h->s).doubles() * sizeof(double);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(A_dev, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STILES_ERR_CUDA;
+  const int rc = launch(h, PLAN_FUSED, A_dev, L_dev, S_dev, scratch, stream);
+  if (rc != STILES_OK) return rc;
+  if (cudaMemcpyAsync(S_host, S_dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return STILES_ERR_CUDA;
+  return STILES_OK;
 }
 
 // Scratch of stiles_factor_selinv_noalloc: one fixed array per device that
@@ -332,7 +351,7 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
       if (value) {
         size_t n = 0;
         for (auto& d : h->dev) n = (size_t)d.ntasks > n ? (size_t)d.ntasks : n;
-        if (cudaMalloc((void**)&h->dtrace, 4 * sizeof(unsigned long long) * (n ? n : 1)) != cudaSuccess)
+        if (cudaMalloc((void**)&h->dtrace, 16 * sizeof(unsigned long long) * (n ? n : 1)) != cudaSuccess)
           return STILES_ERR_OOM;
         h->trace_tasks = n;
       }
@@ -344,10 +363,11 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
 }
 
 extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]) {
-  if (!stats || which < 0 || which > 2 || workers < 1) return STILES_ERR_INVALID_ARG;
+  const int kind = which & 15, prec = which >> 4;
+  if (!stats || kind < 0 || kind > 2 || prec < 0 || prec > PREC_FP32X || workers < 1) return STILES_ERR_INVALID_ARG;
   if (nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
   Plan p;
-  int rc = build_plan(Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow}, (PlanKind)which, workers, &p);
+  int rc = build_plan(Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec}, (PlanKind)kind, workers, &p);
   if (rc) return rc;
   stats[0] = (long long)p.tasks.size();
   stats[1] = (long long)p.segs.size();
@@ -358,6 +378,16 @@ extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, 
   stats[6] = (long long)p.cp_ns;
   stats[7] = (long long)p.makespan_ns;
   return STILES_OK;
+}
+
+extern "C" int stiles_debug_validate(int nt, int b, int band, int arrow, int which) {
+  const int kind = which & 15, prec = which >> 4;
+  if (kind < 0 || kind > 2 || prec < 0 || prec > PREC_FP32X || nt < 1 || b < 1 || band < 0 || arrow < 0)
+    return STILES_ERR_INVALID_ARG;
+  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec};
+  Plan p;
+  int rc = build_plan(sh, (PlanKind)kind, 304, &p);
+  return rc ? rc : validate_plan(p, sh, kind);
 }
 
 extern "C" int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode) {
@@ -406,10 +436,10 @@ extern "C" int stiles_trace(stiles_t h, unsigned long long* out_host, size_t cap
   const size_t n = (size_t)h->dev[h->last_kind].ntasks;
   *n_tasks = n;
   if (!out_host) return STILES_OK;
-  if (capacity < 4 * n) return STILES_ERR_INVALID_ARG;
+  if (capacity < 16 * n) return STILES_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
   if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return STILES_ERR_CUDA;
-  if (n && cudaMemcpy(out_host, h->dtrace, 4 * sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (n && cudaMemcpy(out_host, h->dtrace, 16 * sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
     return STILES_ERR_CUDA;
   return STILES_OK;
 }

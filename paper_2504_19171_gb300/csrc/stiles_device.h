@@ -24,27 +24,32 @@ struct DevStatus {
 //   rem[ntasks]      predecessors not yet finished (image: indeg)
 //   pdone[ntasks]    parts of the task finished so far
 //   slots[nb*kSlotsPerBucket]  bucket b owns slots [b*kSlotsPerBucket, +kSlotsPerBucket)
-//   tail[nbuckets]   pushes into the bucket so far
-//   head[nbuckets]   pops from the bucket so far
-//   gcnt[ngroups]    ready tasks per group of 32 buckets (a scan hint)
+//   tail[nbuckets]   slots reserved by pushes into the bucket so far
+//   head[nbuckets]   slots claimed by pops so far
+//   avail[nbuckets]  parts pushed and not yet claimed (a pop claims one by
+//                    decrementing it while positive, then takes head++)
+//   gcnt[ngroups]    ready parts per group of 32 buckets (a scan hint)
+//   scnt[nsuper]     ready parts per super-group of 32 groups (a scan hint)
 //   uslots[ucap]     urgent queue (critical-path tasks), popped before any bucket
 //   lo[32]           lo[0]: every bucket below it is finished (all popped);
-//                    lo[8]: urgent tail, lo[16]: urgent head
+//                    lo[8]: urgent tail, lo[16]: urgent head, lo[24]: urgent avail
 struct SchedState {
   int* rem;
   int* pdone;
   int* slots;
   int* tail;
   int* head;
+  int* avail;
   int* gcnt;
+  int* scnt;
   int* uslots;
   int* lo;
 };
 
 inline size_t sched_state_ints(int ntasks, int nbuckets, int ucap) {
-  const int ngroups = (nbuckets + 31) / 32;
-  return 2 * (size_t)ntasks + (size_t)nbuckets * kSlotsPerBucket + 2 * (size_t)nbuckets + (size_t)ngroups +
-         (size_t)(ucap > 0 ? ucap : 1) + 32;
+  const int ngroups = (nbuckets + 31) / 32, nsuper = (ngroups + 31) / 32;
+  return 2 * (size_t)ntasks + (size_t)nbuckets * kSlotsPerBucket + 3 * (size_t)nbuckets + (size_t)ngroups +
+         (size_t)nsuper + (size_t)(ucap > 0 ? ucap : 1) + 32;
 }
 
 inline SchedState sched_state_at(int* base, int ntasks, int nbuckets, int ucap) {
@@ -54,8 +59,10 @@ inline SchedState sched_state_at(int* base, int ntasks, int nbuckets, int ucap) 
   s.slots = s.pdone + ntasks;
   s.tail = s.slots + (size_t)nbuckets * kSlotsPerBucket;
   s.head = s.tail + nbuckets;
-  s.gcnt = s.head + nbuckets;
-  s.uslots = s.gcnt + (nbuckets + 31) / 32;
+  s.avail = s.head + nbuckets;
+  s.gcnt = s.avail + nbuckets;
+  s.scnt = s.gcnt + (nbuckets + 31) / 32;
+  s.uslots = s.scnt + ((nbuckets + 31) / 32 + 31) / 32;
   s.lo = s.uslots + (ucap > 0 ? ucap : 1);
   return s;
 }

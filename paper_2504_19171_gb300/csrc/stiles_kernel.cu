@@ -74,14 +74,16 @@ __device__ void check_fail(const KParams& p, int what, long long t, int q) {
   } while (0)
 #endif
 
-// Push a ready task into the bucket of its list-schedule position: one slot
-// per part (value 4 t + part), so that the parts run on different CTAs.
+// Push a ready task into the bucket of its queue position: one slot per part
+// (value 4 t + part), so that the parts run on different CTAs. The slots are
+// reserved (tail), stored, and only then counted as available.
 __device__ __forceinline__ void push_task(const KParams& p, int t) {
   const int parts = p.tasks[t].parts;
   if (p.tasks[t].flags & TF_URGENT) {
     const int pos = atomicAdd(p.q.lo + 8, parts);
     STILES_CHECK(pos + parts <= p.ucap, 1, t, 0);
     for (int q = 0; q < parts; ++q) store_release_i(p.q.uslots + pos + q, 4 * t + q);
+    atomicAdd(p.q.lo + 24, parts);
     return;
   }
   const int b = t / kTasksPerBucket;
@@ -89,88 +91,128 @@ __device__ __forceinline__ void push_task(const KParams& p, int t) {
   const int pos = atomicAdd(p.q.tail + b, parts);
   STILES_CHECK(pos + parts <= p.bcap[b], 3, t, 0);
   for (int q = 0; q < parts; ++q) store_release_i(p.q.slots + (size_t)b * kSlotsPerBucket + pos + q, 4 * t + q);
+  atomicAdd(p.q.avail + b, parts);
   atomicAdd(p.q.gcnt + (b >> 5), parts);
+  atomicAdd(p.q.scnt + (b >> 10), parts);
 }
 
-// Lane 0 of warp 0 pops the ready task part of the earliest bucket
-// (list-schedule order), after the urgent queue. Returns 4 * task + part, or
-// -1 when every part has been popped, the launch was aborted, or this call
-// exceeded the wait budget (TIMEOUT; every path of the loop checks it).
-__device__ int pop_lane0(const KParams& p) {
-  const int nb = p.nbuckets, ngroups = (nb + 31) / 32;
-  const unsigned long long start = gtimer();
-  for (;;) {
+// Lane 0: wait for the store of a claimed queue slot (its pusher reserved it
+// before counting it available, and stores it right after). Returns the
+// item, or -1 on abort / budget expiry.
+__device__ int wait_slot(const KParams& p, int* slot, unsigned long long start) {
+  int t = load_acquire_i(slot);
+  while (t < 0) {
     if (load_relaxed_flag(&p.st->abort)) return -1;
     if (gtimer() - start > (unsigned long long)p.budget_ns) {
-      raise_timeout(p, (long long)load_relaxed_flag(p.q.lo) * kTasksPerBucket);
+      raise_timeout(p, -1);
       return -1;
     }
-    int* slot = nullptr;
-    // urgent queue first (critical-path tasks of the factorization)
-    if (p.ucap > 0) {
-      const int uh = load_relaxed_flag(p.q.lo + 16);
-      if (uh < load_acquire_i(p.q.lo + 8)) {
-        if (atomicCAS(p.q.lo + 16, uh, uh + 1) != uh) continue;  // taken by another worker
-        STILES_CHECK(uh < p.ucap, 4, uh, 0);
-        slot = p.q.uslots + uh;
-      }
-    }
-    if (!slot) {
-      const int l = load_relaxed_flag(p.q.lo);
-      if (l >= nb) {
-        if (load_relaxed_flag(p.q.lo + 16) >= p.ucap) return -1;  // every part popped
-        __nanosleep(200);
-        continue;
-      }
-      // move lo past finished buckets (finished is permanent: atomicMax is safe)
-      int f = l;
-      while (f < nb && f < l + 64 && load_relaxed_flag(p.q.head + f) >= p.bcap[f]) ++f;
-      if (f > l) {
-        atomicMax(p.q.lo, f);
-        continue;
-      }
-      bool raced = false;
-      for (int g = l >> 5; g < ngroups && !slot && !raced; ++g) {
-        if (load_relaxed_flag(p.q.gcnt + g) <= 0) continue;
-        const int b1 = min(nb, 32 * g + 32);
-        for (int b = max(l, 32 * g); b < b1; ++b) {
-          const int h = load_relaxed_flag(p.q.head + b);
-          if (h >= load_acquire_i(p.q.tail + b)) continue;
-          if (atomicCAS(p.q.head + b, h, h + 1) != h) {
-            raced = true;  // another worker took it: rescan from lo
-            break;
-          }
-          atomicSub(p.q.gcnt + g, 1);
-          STILES_CHECK(h < p.bcap[b], 5, b, 0);
-          slot = p.q.slots + (size_t)b * kSlotsPerBucket + h;
-          break;
-        }
-      }
-      if (!slot) {
-        if (!raced) __nanosleep(200);
-        continue;
-      }
-    }
-    // the pusher reserved this slot before storing it: wait for the store
-    int t = load_acquire_i(slot);
-    while (t < 0) {
-      if (load_relaxed_flag(&p.st->abort)) return -1;
-      if (gtimer() - start > (unsigned long long)p.budget_ns) {
-        raise_timeout(p, -1);
-        return -1;
-      }
-      __nanosleep(32);
-      t = load_acquire_i(slot);
-    }
-    return t;
+    __nanosleep(32);
+    t = load_acquire_i(slot);
   }
+  return t;
 }
 
-// Warp 0: lane 0 pops, every lane gets the result.
-__device__ __forceinline__ int pop_task(const KParams& p) {
-  int v = -1;
-  if ((threadIdx.x & 31) == 0) v = pop_lane0(p);
-  return __shfl_sync(0xffffffffu, v, 0);
+// Lane 0: claim one available part of a queue (avail / head pair) without a
+// compare-and-swap retry loop: many idle workers contending for the same
+// bucket each cost two fetch-and-adds, not a round trip per lost race.
+// Returns the claimed slot index, or -1 if nothing was available.
+__device__ __forceinline__ int claim(int* avail, int* head) {
+  if (load_relaxed_flag(avail) <= 0) return -1;
+  if (atomicSub(avail, 1) <= 0) {
+    atomicAdd(avail, 1);
+    return -1;
+  }
+  return atomicAdd(head, 1);
+}
+
+// Lane 0: abort / budget check, then one attempt on the urgent queue.
+// Returns an item (>= 0), -1 to stop, or -3 when no urgent part is ready.
+__device__ int pop_urgent_lane0(const KParams& p, unsigned long long start) {
+  if (load_relaxed_flag(&p.st->abort)) return -1;
+  if (gtimer() - start > (unsigned long long)p.budget_ns) {
+    raise_timeout(p, (long long)load_relaxed_flag(p.q.lo) * kTasksPerBucket);
+    return -1;
+  }
+  if (p.ucap <= 0) return -3;
+  const int uh = claim(p.q.lo + 24, p.q.lo + 16);
+  if (uh < 0) return -3;
+  STILES_CHECK(uh < p.ucap, 4, uh, 0);
+  return wait_slot(p, p.q.uslots + uh, start);
+}
+
+// Warp 0 pops a ready task part: the urgent queue first, then the earliest
+// bucket (queue order) with an available part. Lane 0 takes every decision
+// and broadcasts it, the other lanes only help to scan 32 super-groups /
+// groups / buckets per load round, so the warp stays uniform. Returns
+// 4 * task + part, or -1 when every part has been popped, the launch was
+// aborted, or the wait budget of this call expired (TIMEOUT; checked on
+// every pass of the loop).
+__device__ int pop_task(const KParams& p) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int nb = p.nbuckets, ngroups = (nb + 31) / 32, nsuper = (ngroups + 31) / 32;
+  const unsigned long long start = lane == 0 ? gtimer() : 0ull;
+  for (;;) {
+    int r = -3;
+    if (lane == 0) r = pop_urgent_lane0(p, start);
+    r = __shfl_sync(FULL, r, 0);
+    if (r != -3) return r;
+    int l = 0;
+    if (lane == 0) l = load_relaxed_flag(p.q.lo);
+    l = __shfl_sync(FULL, l, 0);
+    // scan from lo: super-groups of 32 groups, groups of 32 buckets, buckets
+    int got = -3;  // -3: nothing found, -1: stop, >= 0: item
+    const int g_lo = l >> 5;
+    for (int sbase = l >> 10; sbase < nsuper && got == -3; sbase += 32) {
+      const int sg = sbase + lane;
+      unsigned sm = __ballot_sync(FULL, sg < nsuper && load_relaxed_flag(p.q.scnt + sg) > 0);
+      while (sm && got == -3) {
+        const int si = sbase + __ffs(sm) - 1;
+        sm &= sm - 1;
+        const int g = si * 32 + lane;
+        unsigned gm = __ballot_sync(FULL, g < ngroups && g >= g_lo && load_relaxed_flag(p.q.gcnt + g) > 0);
+        while (gm && got == -3) {
+          const int gi = si * 32 + __ffs(gm) - 1;
+          gm &= gm - 1;
+          const int b = gi * 32 + lane;
+          unsigned rm = __ballot_sync(FULL, b < nb && b >= l && load_relaxed_flag(p.q.avail + b) > 0);
+          while (rm && got == -3) {  // try the ready buckets in order
+            const int bb = gi * 32 + __ffs(rm) - 1;
+            rm &= rm - 1;
+            if (lane == 0) {
+              const int h = claim(p.q.avail + bb, p.q.head + bb);
+              if (h >= 0) {
+                atomicSub(p.q.gcnt + gi, 1);
+                atomicSub(p.q.scnt + (gi >> 5), 1);
+                STILES_CHECK(h < p.bcap[bb], 5, bb, 0);
+                got = wait_slot(p, p.q.slots + (size_t)bb * kSlotsPerBucket + h, start);
+              }
+            }
+            got = __shfl_sync(FULL, got, 0);
+          }
+        }
+      }
+    }
+    if (got != -3) return got;
+    // nothing claimed: move lo past finished buckets (finished is permanent,
+    // so atomicMax is safe), stop once every part was popped, else back off
+    if (l >= nb) {
+      int done = 0;
+      if (lane == 0) done = load_relaxed_flag(p.q.lo + 16) >= p.ucap;
+      if (__shfl_sync(FULL, done, 0)) return -1;
+    } else {
+      const int b = l + lane;
+      const bool fin = b >= nb || load_relaxed_flag(p.q.head + b) >= p.bcap[b];
+      const unsigned unf = __ballot_sync(FULL, !fin);
+      const int nfin = unf ? __ffs(unf) - 1 : 32;
+      if (nfin > 0) {
+        if (lane == 0) atomicMax(p.q.lo, l + nfin);
+        continue;
+      }
+    }
+    __nanosleep(200);
+  }
 }
 
 // Warp 0, after task t finished and its writes were fenced: release the
@@ -199,9 +241,15 @@ __device__ __forceinline__ Sub sub_of(const Task& tk, int q) {
     case PM_ROWS4: sb.r0 = 16 * q; sb.rm = min(16, tk.m - sb.r0); break;
     case PM_QUAD4: sb.r0 = 32 * (q & 1); sb.c0 = 32 * (q >> 1); break;
     case PM_TRI3: sb.r0 = q == 0 ? 0 : 32; sb.c0 = q == 2 ? 32 : 0; break;
+    case PM_TILE32: {
+      const int pr = tk.m > 32 ? 2 : 1;
+      sb.r0 = 32 * (q % pr);
+      sb.c0 = 32 * (q / pr);
+      break;
+    }
     default: break;
   }
-  if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3) {
+  if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3 || tk.pmode == PM_TILE32) {
     sb.rm = min(32, tk.m - sb.r0);
     sb.cn = min(32, tk.n - sb.c0);
   }
@@ -229,23 +277,48 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
     const double* B = resolve(p, g.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * g.ldb);
     for (int k0 = 0; k0 < g.k; k0 += KC) {
       const int kc = min(KC, g.k - k0);
-#pragma unroll 4
-      for (int e = tid; e < RM * KC; e += NTHREADS) {
-        int i, kk;
-        if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
-        double v = 0.0;
-        if (i < sb.rm && kk < kc)
-          v = __ldcg(ta ? A + (int64_t)(k0 + kk) + (int64_t)i * g.lda : A + (int64_t)i + (int64_t)(k0 + kk) * g.lda);
-        As[kk * LDS + i] = v;
+      // each batch of loads is in flight before its shared-memory stores
+      constexpr int NA = RM * KC / NTHREADS, NB = CN * KC / NTHREADS;
+      constexpr int BA = NA < 8 ? NA : 8, BB = NB < 8 ? NB : 8;
+#pragma unroll
+      for (int u0 = 0; u0 < NA; u0 += BA) {
+        double v[BA];
+#pragma unroll
+        for (int u = 0; u < BA; ++u) {
+          const int e = tid + (u0 + u) * NTHREADS;
+          int i, kk;
+          if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
+          v[u] = (i < sb.rm && kk < kc)
+                     ? __ldcg(ta ? A + (int64_t)(k0 + kk) + (int64_t)i * g.lda : A + (int64_t)i + (int64_t)(k0 + kk) * g.lda)
+                     : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < BA; ++u) {
+          const int e = tid + (u0 + u) * NTHREADS;
+          int i, kk;
+          if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
+          As[kk * LDS + i] = v[u];
+        }
       }
-#pragma unroll 4
-      for (int e = tid; e < CN * KC; e += NTHREADS) {
-        int j, kk;
-        if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
-        double v = 0.0;
-        if (j < sb.cn && kk < kc)
-          v = __ldcg(tb ? B + (int64_t)j + (int64_t)(k0 + kk) * g.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * g.ldb);
-        Bs[kk * LDS + j] = v;
+#pragma unroll
+      for (int u0 = 0; u0 < NB; u0 += BB) {
+        double v[BB];
+#pragma unroll
+        for (int u = 0; u < BB; ++u) {
+          const int e = tid + (u0 + u) * NTHREADS;
+          int j, kk;
+          if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
+          v[u] = (j < sb.cn && kk < kc)
+                     ? __ldcg(tb ? B + (int64_t)j + (int64_t)(k0 + kk) * g.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * g.ldb)
+                     : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < BB; ++u) {
+          const int e = tid + (u0 + u) * NTHREADS;
+          int j, kk;
+          if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
+          Bs[kk * LDS + j] = v[u];
+        }
       }
       __syncthreads();
 #pragma unroll 8
@@ -265,6 +338,298 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
   }
 }
 
+// FP32-class products: operands rounded to FP32 while staged, FP32 FMA
+// accumulation, result returned in FP64 (same thread mapping as accumulate).
+template <int TM, int TN>
+__device__ __forceinline__ void accumulate_f32(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[TM][TN],
+                                               double* smem) {
+  constexpr int RM = 16 * TM, CN = 8 * TN, LF = FB + 1;
+  float* As = reinterpret_cast<float*>(smem);
+  float* Bs = As + KC * LF;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float f[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) f[i][j] = 0.0f;
+  for (int s = 0; s < tk.nseg; ++s) {
+    const Seg g = p.segs[tk.seg0 + s];
+    const bool ta = g.trans & 1, tb = g.trans & 2;
+    const double* A = resolve(p, g.a) + (ta ? (int64_t)sb.r0 * g.lda : (int64_t)sb.r0);
+    const double* B = resolve(p, g.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * g.ldb);
+    for (int k0 = 0; k0 < g.k; k0 += KC) {
+      const int kc = min(KC, g.k - k0);
+      // all loads of this thread for the chunk are in flight before any is stored
+      constexpr int NA = RM * KC / NTHREADS, NB = CN * KC / NTHREADS;
+      float fa[NA], fb[NB];
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        const int e = tid + u * NTHREADS;
+        int i, kk;
+        if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
+        fa[u] = (i < sb.rm && kk < kc)
+                    ? (float)__ldcg(ta ? A + (int64_t)(k0 + kk) + (int64_t)i * g.lda : A + (int64_t)i + (int64_t)(k0 + kk) * g.lda)
+                    : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int e = tid + u * NTHREADS;
+        int j, kk;
+        if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
+        fb[u] = (j < sb.cn && kk < kc)
+                    ? (float)__ldcg(tb ? B + (int64_t)j + (int64_t)(k0 + kk) * g.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * g.ldb)
+                    : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        const int e = tid + u * NTHREADS;
+        int i, kk;
+        if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
+        As[kk * LF + i] = fa[u];
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int e = tid + u * NTHREADS;
+        int j, kk;
+        if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
+        Bs[kk * LF + j] = fb[u];
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < KC; ++kk) {
+        float a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk * LF + tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk * LF + ty + 8 * j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) f[i][j] = fmaf(a[i], b[j], f[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (double)f[i][j];
+}
+
+// ---- emulated FP64 on the tensor cores (split-precision integer digits) --
+//
+// Error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump: for one
+// segment, every row i of op(A) gets the exponent E_i of its largest entry
+// and every column j of op(B) the exponent F_j; each entry becomes a 48-bit
+// fixed-point integer relative to that exponent, cut into EMU_S = 6 signed
+// 8-bit digits, which bf16 holds exactly. A product of two digits is an exact
+// 16-bit integer; a sum of at most 6 x 32 of them stays below 2^24, so the
+// FP32 tensor-core accumulation of one K chunk is exact and is moved into an
+// int32 accumulator per level L = t + u (digit weights 2^-8t, 2^-8u). Levels
+// L <= EMU_S - 1 are kept (the rest weigh less than 2^-48 relative), and the
+// levels are recombined in FP64 with the scale 2^(E_i + F_j) at the end.
+constexpr int EMU_S = 6;
+constexpr int EMU_KP = 40;  // padded digit-row length (bf16) in shared memory
+
+__device__ __forceinline__ int biased_exp(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+}
+
+// The EMU_S digits of v relative to the biased exponent emax (>= that of v),
+// as bf16 bit patterns (sign applied to every digit).
+__device__ __forceinline__ void emu_digits(double v, int emax, uint16_t (&d)[EMU_S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const int shift = 5 + emax - (e ? e : 1);
+  const unsigned long long X = shift >= 64 ? 0ull : (m >> shift);  // < 2^48
+  const uint16_t sgn = (uint16_t)((bits >> 48) & 0x8000u);
+#pragma unroll
+  for (int t = 0; t < EMU_S; ++t) {
+    const unsigned dt = (unsigned)(X >> (8 * (EMU_S - 1 - t))) & 0xffu;
+    // exact float of an 8-bit integer, then its upper 16 bits (= its bf16)
+    const float f = __uint_as_float(0x4B000000u | dt) - 8388608.0f;
+    d[t] = dt ? (uint16_t)((__float_as_uint(f) >> 16) | sgn) : (uint16_t)0;
+  }
+}
+
+// out[i] = largest biased exponent over k < K of element (i, k) of a panel of
+// n <= 32 vectors: element (i, k) sits at P[i + k ld] when `along_i` (the
+// vectors' index is the contiguous one), else at P[k + i ld]. Loads follow
+// the contiguous dimension; out[] gets every i < 32 (0 beyond n).
+__device__ __forceinline__ void emu_max_exp(const double* P, int ld, bool along_i, int n, int K, int* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (along_i) {  // lanes over i, warps over k
+    int mx = 0;
+    if (lane < n)
+      for (int k = warp; k < K; k += 4) mx = max(mx, biased_exp(__ldcg(P + lane + (int64_t)k * ld)));
+    __shared__ int part[4][32];
+    part[warp][lane] = mx;
+    __syncthreads();
+    if (warp == 0) out[lane] = max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane]));
+    __syncthreads();
+  } else {  // one warp per vector, lanes over k
+    for (int i = warp; i < 32; i += 4) {
+      int mx = 0;
+      if (i < n)
+        for (int k = lane; k < K; k += 32) mx = max(mx, biased_exp(__ldcg(P + k + (int64_t)i * ld)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) out[i] = mx;
+    }
+  }
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Sub-tile of at most 32 x 32; returns the products in the accumulate<2,4>
+// thread mapping (through shared memory).
+__device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[2][4], double* smem) {
+  uint16_t* Ad = reinterpret_cast<uint16_t*>(smem);  // [EMU_S][32][EMU_KP]
+  uint16_t* Bd = Ad + EMU_S * 32 * EMU_KP;            // [EMU_S][32][EMU_KP]
+  int* rexp = reinterpret_cast<int*>(smem + 2 * KC * LDS);  // X region: exponents, level sums, result
+  int* cexp = rexp + 32;
+  int* lev = cexp + 32;  // [EMU_S * 8][NTHREADS] int32 level accumulators (per thread, conflict-free)
+  double* R = smem + 2 * KC * LDS + 32;  // 32 x 33 result scatter (after the level sums are consumed)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3, wr = warp & 1, wc = warp >> 1;
+  double res[2][4];  // rows 16 wr + g + 8 h (h = q >> 1), cols 16 wc + 8 j + 2 tq + (q & 1)
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) res[j][q] = 0.0;
+  for (int s = 0; s < tk.nseg; ++s) {
+    const Seg gs = p.segs[tk.seg0 + s];
+    const bool ta = gs.trans & 1, tb = gs.trans & 2;
+    const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
+    const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
+    // exponents of the largest entry of every row of op(A) / column of op(B),
+    // read along each operand's contiguous dimension
+    emu_max_exp(A, gs.lda, !ta, sb.rm, gs.k, rexp);
+    emu_max_exp(B, gs.ldb, tb, sb.cn, gs.k, cexp);
+    __syncthreads();
+    // int32 level sums stay exact for 6 * 4096 * 255^2 < 2^31: recombine every 4096 of K
+    for (int kb = 0; kb < gs.k; kb += 4096) {
+      const int kend = min(gs.k, kb + 4096);
+#pragma unroll
+      for (int x = 0; x < EMU_S * 8; ++x) lev[x * NTHREADS + tid] = 0;
+      for (int k0 = kb; k0 < kend; k0 += KC) {
+        const int kc = min(KC, kend - k0);
+        // stage the digits of op(A)[0:32, k0:k0+32] and op(B)[k0:k0+32, 0:32]:
+        // all 16 loads of this thread are issued before any is used
+        constexpr int NE = 32 * KC / NTHREADS;
+        double va[NE], vb[NE];
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+          const int e = tid + u * NTHREADS;
+          int i, kk;
+          if (!ta) { i = e & 31; kk = e >> 5; } else { kk = e & 31; i = e >> 5; }
+          va[u] = (i < sb.rm && kk < kc)
+                      ? __ldcg(ta ? A + (int64_t)(k0 + kk) + (int64_t)i * gs.lda : A + (int64_t)i + (int64_t)(k0 + kk) * gs.lda)
+                      : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+          const int e = tid + u * NTHREADS;
+          int j, kk;
+          if (tb) { j = e & 31; kk = e >> 5; } else { kk = e & 31; j = e >> 5; }
+          vb[u] = (j < sb.cn && kk < kc)
+                      ? __ldcg(tb ? B + (int64_t)j + (int64_t)(k0 + kk) * gs.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * gs.ldb)
+                      : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+          const int e = tid + u * NTHREADS;
+          int i, kk;
+          if (!ta) { i = e & 31; kk = e >> 5; } else { kk = e & 31; i = e >> 5; }
+          uint16_t d[EMU_S];
+          emu_digits(va[u], rexp[i], d);
+#pragma unroll
+          for (int t = 0; t < EMU_S; ++t) Ad[(t * 32 + i) * EMU_KP + kk] = d[t];
+        }
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+          const int e = tid + u * NTHREADS;
+          int j, kk;
+          if (tb) { j = e & 31; kk = e >> 5; } else { kk = e & 31; j = e >> 5; }
+          uint16_t d[EMU_S];
+          emu_digits(vb[u], cexp[j], d);
+#pragma unroll
+          for (int t = 0; t < EMU_S; ++t) Bd[(t * 32 + j) * EMU_KP + kk] = d[t];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int L = 0; L < EMU_S; ++L) {
+          float f[2][4] = {};
+#pragma unroll
+          for (int t = 0; t <= L; ++t) {
+            const int u = L - t;
+#pragma unroll
+            for (int ks = 0; ks < KC; ks += 16) {
+              const uint16_t* ap = Ad + (t * 32 + 16 * wr + g) * EMU_KP + ks + 2 * tq;
+              uint32_t a[4];
+              a[0] = *reinterpret_cast<const uint32_t*>(ap);
+              a[1] = *reinterpret_cast<const uint32_t*>(ap + 8 * EMU_KP);
+              a[2] = *reinterpret_cast<const uint32_t*>(ap + 8);
+              a[3] = *reinterpret_cast<const uint32_t*>(ap + 8 * EMU_KP + 8);
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                const uint16_t* bp = Bd + (u * 32 + 16 * wc + 8 * j + g) * EMU_KP + ks + 2 * tq;
+                mma_bf16(f[j], a, *reinterpret_cast<const uint32_t*>(bp), *reinterpret_cast<const uint32_t*>(bp + 8));
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lev[(L * 8 + j * 4 + q) * NTHREADS + tid] += __float2int_rn(f[j][q]);
+        }
+        __syncthreads();
+      }
+      // recombine exactly in 128-bit integers: V = sum_L lev_L 2^(8 (EMU_S - 1 - L)),
+      // then one rounding to FP64 and the scale 2^(E_i + F_j - 2140 + 8 (EMU_S - 1))
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          __int128 V = 0;
+#pragma unroll
+          for (int L = 0; L < EMU_S; ++L)
+            V += (__int128)lev[(L * 8 + j * 4 + q) * NTHREADS + tid] * ((__int128)1 << (8 * (EMU_S - 1 - L)));
+          const long long vh = (long long)(V >> 64);
+          const unsigned long long vl = (unsigned long long)V;
+          const double v = fma((double)vh, 18446744073709551616.0, (double)vl);
+          const int row = 16 * wr + g + 8 * (q >> 1), col = 16 * wc + 8 * j + 2 * tq + (q & 1);
+          const int k2 = rexp[row] + cexp[col] - 2140 + 8 * (EMU_S - 1);
+          // 2^k2 built from its exponent bits when it is a normal double
+          const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
+          res[j][q] = fma(v, sc, res[j][q]);
+        }
+    }
+    __syncthreads();
+  }
+  // scatter to the accumulate<2,4> mapping: rows tx + 16 i, columns ty + 8 jj
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int row = 16 * wr + g + 8 * (q >> 1), col = 16 * wc + 8 * j + 2 * tq + (q & 1);
+      R[row * 33 + col] = res[j][q];
+    }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = R[(tx + 16 * i) * 33 + ty + 8 * jj];
+  __syncthreads();
+}
+
 // X[rl][cl] = sign * acc (or cin - acc) over the whole (16 TM) x (8 TN) sub-tile
 // (rows / columns beyond the sub-tile get -acc = 0 or are ignored later).
 template <int TM, int TN>
@@ -272,22 +637,45 @@ __device__ __forceinline__ void acc_to_smem(const KParams& p, const Task& tk, co
                                             double* X, bool sub_cin, double sign) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const double* C = sub_cin ? resolve(p, tk.cin) + sb.r0 + (int64_t)sb.c0 * tk.ldc : nullptr;
+  // every load is issued before the first shared-memory store (a store
+  // through a generic pointer would otherwise order the loads one by one)
+  double v[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int r = tx + 16 * i, c = ty + 8 * j;
-      double v = sign * acc[i][j];
-      if (sub_cin && r < sb.rm && c < sb.cn) v = __ldcg(C + r + (int64_t)c * tk.ldc) - acc[i][j];
-      X[r * LDS + c] = v;
+      v[i][j] = (sub_cin && r < sb.rm && c < sb.cn) ? __ldcg(C + r + (int64_t)c * tk.ldc) : 0.0;
+    }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int r = tx + 16 * i, c = ty + 8 * j;
+      const bool in = sub_cin && r < sb.rm && c < sb.cn;
+      X[r * LDS + c] = in ? v[i][j] - acc[i][j] : sign * acc[i][j];
     }
 }
 
+// T[r][c] = lower triangle of the dim x dim block at tk.aux (zero above):
+// thread t reads rows t % 64 of columns t / 64, +2, +4, ... in batches of 8
+// loads in flight before their shared-memory stores.
 __device__ __forceinline__ void load_tri(const KParams& p, const Task& tk, int dim, double* T) {
   const double* S = resolve(p, tk.aux);
-  for (int e = threadIdx.x; e < dim * dim; e += NTHREADS) {
-    const int r = e % dim, c = e / dim;
-    T[r * LDS + c] = (r >= c) ? __ldcg(S + r + (int64_t)c * tk.ldx) : 0.0;
+  const int r = threadIdx.x & (FB - 1), c0 = threadIdx.x / FB;
+  constexpr int kStep = NTHREADS / FB, kBatch = 8;
+  for (int cb = c0; cb < FB; cb += kStep * kBatch) {
+    double v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int c = cb + u * kStep;
+      v[u] = (r < dim && c < dim && r >= c) ? __ldcg(S + r + (int64_t)c * tk.ldx) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int c = cb + u * kStep;
+      if (r < dim && c < dim) T[r * LDS + c] = v[u];
+    }
   }
 }
 
@@ -344,64 +732,75 @@ __device__ __forceinline__ void trsm_cols_ln(double* X, const double* T, const d
   }
 }
 
-// In-place lower Cholesky of the n x n block X (n <= FB), right-looking in
-// panels of 16 columns: warp 0 factors the 16 x 16 diagonal part, all threads
-// solve the panel below it (a column sweep: rows in parallel) and update the
-// trailing lower triangle. A pivot d gives r = rsqrt(d) (one dependent FP64
-// chain instead of sqrt then a divide; dependent FP64 operations cost about
-// 64 cycles each on GB300), L_jj = d r and the column is scaled by r.
-// `rcp` is a scratch column of at least FB doubles (stride LDS). Returns the
-// first column (0-based) whose pivot was not positive, or -1.
-__device__ int potrf_smem(double* X, int n, double* rcp) {
-  const int tid = threadIdx.x, lane = tid & 31;
+// In-place lower Cholesky of the n x n block X (n <= FB), one column per
+// step with a two-column lookahead, so that a step has one block barrier:
+//   warp 0, step j: pivot d = X[j][j], r = rsqrt(d) (one dependent FP64
+//     chain instead of sqrt then a divide), L_jj = d r, column j scaled by r,
+//     then column j+1 updated by columns j-1 and j (it is pivot j+1 next);
+//   warps 1-3, step j: columns j+2 .. n-1 (lower part) updated by column j-1.
+// Every column thus receives the updates of the columns before it in
+// ascending order, and only warp 0's pivot chain is on the critical path.
+// The warps 1-3 rank-1 update walks the lower triangle of width w as w/2
+// row pairs (a, w-1-a) of w+1 elements each, so no lane idles.
+// Returns the first column (0-based) whose pivot was not positive, or -1.
+__device__ int potrf_smem(double* X, int n) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int s_bad;
-  if (tid == 0) s_bad = -1;
-  for (int p0 = 0; p0 < n; p0 += 16) {
-    const int pw = min(16, n - p0);
-    if (tid < 32) {
-      for (int j = 0; j < pw; ++j) {
-        const int cj = p0 + j;
-        const double d = X[cj * LDS + cj];
-        const double rl = rsqrt(d);
-        __syncwarp();
-        if (lane == 0) {
-          if (!(d > 0.0) && s_bad < 0) s_bad = cj;
-          X[cj * LDS + cj] = d * rl;
-          rcp[cj * LDS] = rl;
-        }
-        if (lane > j && lane < pw) X[(p0 + lane) * LDS + cj] *= rl;
-        __syncwarp();
-        const int w = pw - j - 1;
-        for (int e = lane; e < w * w; e += 32) {
-          const int r = j + 1 + e % w, c = j + 1 + e / w;
-          if (c <= r) X[(p0 + r) * LDS + p0 + c] -= X[(p0 + r) * LDS + cj] * X[(p0 + c) * LDS + cj];
-        }
-        __syncwarp();
+  int bad = -1;
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      const double d = X[j * LDS + j];
+      const double rr = rsqrt(d);
+      if (lane == 0) {
+        if (!(d > 0.0) && bad < 0) bad = j;
+        X[j * LDS + j] = d * rr;
       }
-    }
-    __syncthreads();
-    // rows below the panel: X[r][p0:p0+pw] <- X[r][p0:p0+pw] D^{-T} (rows in parallel)
-    const int t0 = p0 + pw, w = n - t0;
-    for (int j = 0; j < pw; ++j) {
-      for (int r = t0 + tid; r < n; r += NTHREADS) X[r * LDS + p0 + j] *= rcp[(p0 + j) * LDS];
-      __syncthreads();
-      for (int e = tid; e < w * (pw - j - 1); e += NTHREADS) {
-        const int r = t0 + e % w, c = p0 + j + 1 + e / w;
-        X[r * LDS + c] -= X[r * LDS + p0 + j] * X[c * LDS + p0 + j];
+      for (int r = j + 1 + lane; r < n; r += 32) X[r * LDS + j] *= rr;
+      __syncwarp();
+      if (j + 1 < n) {
+        const int j1 = j + 1;
+        const double l1 = X[j1 * LDS + j];
+        const double l0 = j > 0 ? X[j1 * LDS + j - 1] : 0.0;
+        for (int r = j1 + lane; r < n; r += 32) {
+          double x = X[r * LDS + j1];
+          if (j > 0) x = fma(-X[r * LDS + j - 1], l0, x);
+          X[r * LDS + j1] = fma(-X[r * LDS + j], l1, x);
+        }
       }
-      __syncthreads();
-    }
-    // trailing lower triangle: X[r][c] -= sum_k X[r][p0+k] X[c][p0+k]
-    for (int e = tid; e < w * w; e += NTHREADS) {
-      const int r = t0 + e % w, c = t0 + e / w;
-      if (c <= r) {
-        double sacc = 0.0;
-        for (int k = 0; k < pw; ++k) sacc = fma(X[r * LDS + p0 + k], X[c * LDS + p0 + k], sacc);
-        X[r * LDS + c] -= sacc;
+    } else if (j > 0 && j + 2 < n) {
+      const int c0 = j + 2, w = n - c0, w1 = w + 1, k = j - 1;
+      const int t = tid - 32, nt = NTHREADS - 32;
+      const int di = nt / w1, dk = nt % w1;
+      int i = t / w1, kk = t % w1;
+      constexpr int B = 6;  // elements per batch: their loads are issued before their stores
+      for (int e = t; e < w * w1 / 2; e += B * nt) {
+        int idx[B];
+        double xr[B], lr[B], lc[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          const int a = kk <= i ? i : w - 1 - i, b = kk <= i ? kk : kk - i - 1;
+          idx[u] = e + u * nt < w * w1 / 2 ? (c0 + a) * LDS + c0 + b : -1;
+          if (idx[u] >= 0) {
+            xr[u] = X[idx[u]];
+            lr[u] = X[(c0 + a) * LDS + k];
+            lc[u] = X[(c0 + b) * LDS + k];
+          }
+          kk += dk;
+          i += di;
+          if (kk >= w1) {
+            kk -= w1;
+            ++i;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+          if (idx[u] >= 0) X[idx[u]] = fma(-lr[u], lc[u], xr[u]);
       }
     }
     __syncthreads();
   }
+  if (tid == 0) s_bad = bad;
+  __syncthreads();
   return s_bad;
 }
 
@@ -414,7 +813,15 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m = tk.m, n = tk.n;
   double acc[TM][TN];
-  if (tk.op != OP_TRTRI) accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
+  if (tk.op != OP_TRTRI) {
+    if (tk.prec == PREC_EMU64) {
+      if constexpr (TM == 2 && TN == 4) accumulate_emu(p, tk, sb, acc, smem);
+    } else if (tk.prec == PREC_FP32X) {
+      accumulate_f32<TM, TN>(p, tk, sb, acc, smem);
+    } else {
+      accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
+    }
+  }
 
   switch (tk.op) {
     case OP_UPD:
@@ -482,7 +889,7 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
           case OP_POTRF: {
             acc_to_smem<TM, TN>(p, tk, sb, acc, X, true, 1.0);
             __syncthreads();
-            const int bad = potrf_smem(X, n, T);
+            const int bad = potrf_smem(X, n);
             store_sub(p, tk, sb, X, true);
             if (tk.zrows > 0) {  // strict upper part of L's diagonal tile in this block column
               double* Z = resolve(p, tk.out) - tk.zrows;
@@ -589,7 +996,8 @@ __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double*
     case PM_ROWS2: run_sub<2, 8>(p, tk, sb, smem); break;
     case PM_ROWS4: run_sub<1, 8>(p, tk, sb, smem); break;
     case PM_QUAD4:
-    case PM_TRI3: run_sub<2, 4>(p, tk, sb, smem); break;
+    case PM_TRI3:
+    case PM_TILE32: run_sub<2, 4>(p, tk, sb, smem); break;
     default: run_sub<4, 8>(p, tk, sb, smem); break;
   }
 }
@@ -636,16 +1044,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
       __syncwarp();
       if (s_last) {
         complete_task(p, t);
-        if (threadIdx.x == 0) {
-          atomicAdd(&p.st->done, 1ull);
-          if (p.trace) {
-            unsigned long long* tr = p.trace + 4 * (size_t)t;
-            tr[0] = t_claim;
-            tr[1] = t_ready;
-            tr[2] = gtimer();
-            tr[3] = ((unsigned long long)smid() << 32) | ((unsigned long long)blockIdx.x << 8) | tk.op;
-          }
-        }
+        if (threadIdx.x == 0) atomicAdd(&p.st->done, 1ull);
+      }
+      if (p.trace && threadIdx.x == 0) {  // one record per task part
+        unsigned long long* tr = p.trace + 4 * (4 * (size_t)t + q);
+        tr[0] = t_claim;
+        tr[1] = t_ready;
+        tr[2] = gtimer();
+        tr[3] = ((unsigned long long)smid() << 32) | ((unsigned long long)blockIdx.x << 12) |
+                ((unsigned long long)tk.prec << 10) | ((unsigned long long)s_last << 9) |
+                ((unsigned long long)(tk.flags & TF_URGENT) << 7) | tk.op;
       }
     }
   }

@@ -33,6 +33,8 @@ STILES_ERR_PLAN = -7
 STILES_ERR_TOO_LARGE = -8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 STILES_FP64 = 0
+STILES_EMU64 = 1
+STILES_FP32X = 2
 STILES_OPT_WAIT_BUDGET_NS = 1
 STILES_OPT_GRID = 2
 STILES_OPT_TRACE = 3
@@ -43,7 +45,7 @@ EXPORTS = [
     "stiles_create", "stiles_layout_doubles", "stiles_workspace_bytes", "stiles_factor", "stiles_selinv",
     "stiles_factor_selinv", "stiles_logdet", "stiles_status", "stiles_set_option", "stiles_plan_stats",
     "stiles_debug_check_corrupted", "stiles_debug_break_plan", "stiles_destroy", "stiles_strerror", "stiles_trace",
-    "stiles_factor_selinv_noalloc",
+    "stiles_factor_selinv_noalloc", "stiles_debug_validate", "stiles_factor_selinv_host",
 ]
 
 
@@ -76,6 +78,8 @@ def _load() -> ctypes.CDLL:
         "stiles_strerror": [i32],
         "stiles_trace": [vp, P(ctypes.c_ulonglong), sz, P(sz)],
         "stiles_factor_selinv_noalloc": [vp, vp, vp, vp, vp],
+        "stiles_debug_validate": [i32, i32, i32, i32, i32],
+        "stiles_factor_selinv_host": [vp, vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -127,6 +131,14 @@ def stiles_factor_selinv(h: int, A_ptr: int, L_ptr: int, S_ptr: int, scratch_ptr
     _check(_lib.stiles_factor_selinv(h, A_ptr, L_ptr, S_ptr, scratch_ptr, stream), "stiles_factor_selinv")
 
 
+def stiles_factor_selinv_host(h: int, A_host_ptr: int, S_host_ptr: int, A_ptr: int, L_ptr: int, S_ptr: int,
+                              scratch_ptr: int, stream: int = 0) -> None:
+    """H2D copy of the packed A, fused factor + selected inversion, D2H copy
+    of Sigma, all enqueued on `stream` by the library."""
+    _check(_lib.stiles_factor_selinv_host(h, A_host_ptr, S_host_ptr, A_ptr, L_ptr, S_ptr, scratch_ptr, stream),
+           "stiles_factor_selinv_host")
+
+
 def stiles_factor_selinv_noalloc(h: int, A_ptr: int, L_ptr: int, S_ptr: int, stream: int = 0) -> None:
     """Factor + selected inversion without any device allocation: the scratch
     is the library's fixed 64 MiB array (shared by all calls; see the C
@@ -152,11 +164,16 @@ def stiles_set_option(h: int, option: int, value: int) -> None:
     _check(_lib.stiles_set_option(h, option, int(value)), "stiles_set_option")
 
 
-def stiles_plan_stats(nt: int, b: int, band: int, arrow: int, which: int, workers: int = 152) -> Dict[str, int]:
+def stiles_plan_stats(nt: int, b: int, band: int, arrow: int, which: int, workers: int = 152,
+                      precision: int = STILES_FP64) -> Dict[str, int]:
     st = (ctypes.c_longlong * 8)()
-    _check(_lib.stiles_plan_stats(nt, b, band, arrow, which, workers, st), "stiles_plan_stats")
+    _check(_lib.stiles_plan_stats(nt, b, band, arrow, which + 16 * precision, workers, st), "stiles_plan_stats")
     keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns"]
     return dict(zip(keys, list(st)))
+
+
+def stiles_debug_validate(nt: int, b: int, band: int, arrow: int, which: int, precision: int = STILES_FP64) -> int:
+    return _lib.stiles_debug_validate(nt, b, band, arrow, which + 16 * precision)
 
 
 def stiles_debug_check_corrupted(nt: int, b: int, band: int, arrow: int, which: int, mode: int) -> int:
@@ -168,11 +185,12 @@ def stiles_debug_break_plan(h: int, which: int) -> None:
 
 
 def stiles_trace(h: int) -> np.ndarray:
-    """Per-task trace of the last launch as an (n, 4) uint64 array: claim,
-    ready and end times (ns) and (sm << 32 | cta << 8 | op)."""
+    """Per-part trace of the last launch as an (n_tasks, 4 parts, 4) uint64
+    array: search start, got-part and end times (ns) and the packed
+    (sm, cta, precision, last part, urgent, op) word; absent parts are zero."""
     n = ctypes.c_size_t()
     _check(_lib.stiles_trace(h, None, 0, ctypes.byref(n)), "stiles_trace")
-    out = np.zeros((n.value, 4), dtype=np.uint64)
+    out = np.zeros((n.value, 4, 4), dtype=np.uint64)
     _check(_lib.stiles_trace(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), out.size, ctypes.byref(n)),
            "stiles_trace")
     return out
@@ -240,7 +258,8 @@ class PackedLayout:
 class Stiles:
     """One handle plus its device buffers (torch float64 tensors on CUDA)."""
 
-    def __init__(self, nt: int, b: int, band: int, arrow: int, device: str = "cuda", wait_budget_s: float = None):
+    def __init__(self, nt: int, b: int, band: int, arrow: int, device: str = "cuda", wait_budget_s: float = None,
+                 precision: int = STILES_FP64):
         import torch
 
         if not torch.cuda.is_available():
@@ -248,7 +267,7 @@ class Stiles:
         self.torch = torch
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
-            self.h = stiles_create(nt, b, band, arrow, STILES_FP64)
+            self.h = stiles_create(nt, b, band, arrow, precision)
         self.layout = PackedLayout(nt, b, band, arrow)
         self.nt, self.b, self.w, self.a = nt, b, self.layout.w, arrow
         Lb, Sb, Wb = stiles_workspace_bytes(self.h)
@@ -290,11 +309,11 @@ class Stiles:
         torch = self.torch
         if self.A is None:
             self.A = torch.empty(self.doubles, dtype=torch.float64, device=self.device)
-        s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        with torch.cuda.stream(s):
-            self.A.copy_(A_host, non_blocking=True)
-            self.factor_selinv(stream=s)
-            S_host.copy_(self.S, non_blocking=True)
+        for t in (A_host, S_host):
+            if t.dtype != torch.float64 or t.device.type != "cpu" or not t.is_contiguous() or t.numel() != self.doubles:
+                raise ValueError("host buffers must be contiguous CPU float64 tensors of the packed layout size")
+        stiles_factor_selinv_host(self.h, A_host.data_ptr(), S_host.data_ptr(), self.A.data_ptr(), self.L.data_ptr(),
+                                  self.S.data_ptr(), self.scratch.data_ptr(), self.stream_ptr(stream))
         return self.logdet()
 
     def status(self) -> Tuple[int, int, int]:

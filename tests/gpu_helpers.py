@@ -22,12 +22,12 @@ def rel_err(got: dict, ref: dict) -> float:
     return num / den if den > 0 else num
 
 
-def run_gpu(M, mode="fused", budget_s=5.0):
+def run_gpu(M, mode="fused", budget_s=5.0, precision=0):
     """Factor and invert M on the GPU. Returns (L tiles, Sigma tiles,
     logdet, (code, info, done))."""
     S = need_gpu()
     import torch
-    st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=budget_s).upload(M)
+    st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=budget_s, precision=precision).upload(M)
     try:
         if mode == "fused":
             st.factor_selinv()

@@ -95,3 +95,16 @@ def test_packed_layout_roundtrip(S):
     # column-major inside a tile, fixed column stride
     assert lay.offset(1, 0) == 49 and lay.offset(5, 0) == 3 * 49 and lay.offset(1, 1) == lay.colstride
     assert flat[1] == M.tiles[(0, 0)][1, 0]
+
+
+VALIDATE_SHAPES = [(16, 64, 1, 16), (5, 100, 2, 37), (9, 130, 1, 70), (4, 3, 1, 2), (1, 50, 0, 5), (6, 64, 0, 0),
+                   (7, 40, 4, 0), (3, 200, 2, 1), (12, 64, 3, 64), (30, 1, 1, 0), (10, 2, 3, 1), (6, 100, 1, 9)]
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_plans_validate_on_host(S, which, precision):
+    """Host emulation of one launch: in-bounds accesses of every task part,
+    queue capacities, every task released once."""
+    for shape in VALIDATE_SHAPES:
+        assert S.stiles_debug_validate(*shape, which, precision) == S.STILES_OK, shape

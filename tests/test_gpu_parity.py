@@ -85,3 +85,73 @@ def test_bitwise_repeatable():
     for key in S1:
         assert np.array_equal(S1[key], S2[key]) and np.array_equal(S1[key], S3[key])
     assert ld1 == ld2 == ld3
+
+
+
+@pytest.mark.gpu
+def test_host_buffer_entry_point():
+    """stiles_factor_selinv_host (H2D of A, launch, D2H of Sigma on one
+    stream) returns the same bits as the device-buffer call, and Sigma
+    matches the oracle."""
+    import torch
+    M = W.random_arrowhead(9, 96, 2, 20, seed=21)
+    _, S_dev, ld_dev, _ = run_gpu(M, "fused")
+    S = need_gpu()
+    st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=5.0)
+    try:
+        A_host = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).pin_memory()
+        S_host = torch.full((st.doubles,), np.nan, dtype=torch.float64).pin_memory()
+        ld = st.factor_selinv_host(A_host, S_host)
+        assert st.status()[0] == S.STILES_OK
+        got = st.layout.unpack(S_host.numpy())
+    finally:
+        st.close()
+    for key in S_dev:
+        assert np.array_equal(got[key], S_dev[key])
+    assert ld == ld_dev
+    _, Sref, _ = O.selinv(M)
+    assert rel_err(got, Sref) < FP64_TOL
+
+EMU_TOL = 1e-12  # emulated-FP64 target against the FP64 oracle
+PREC_SHAPES = [(16, 64, 1, 16), (5, 100, 2, 37), (9, 130, 1, 70), (4, 3, 1, 2), (7, 40, 4, 0), (12, 64, 3, 64)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", PREC_SHAPES)
+@pytest.mark.parametrize("mode", ["fused", "split"])
+def test_emulated_fp64_parity(shape, mode):
+    S = need_gpu()
+    M = W.random_arrowhead(*shape, seed=sum(shape) + 1)
+    Lr, Sr, ldr = O.selinv(M)
+    L, Sg, ld, status = run_gpu(M, mode, precision=S.STILES_EMU64)
+    assert status[0] == 0
+    assert rel_err(L, Lr) < EMU_TOL
+    assert rel_err(Sg, Sr) < EMU_TOL
+    assert abs(ld - ldr) < EMU_TOL * max(1.0, abs(ldr))
+    for i in range(M.nt + (1 if M.a else 0)):
+        assert np.array_equal(Sg[(i, i)], Sg[(i, i)].T)
+
+
+@pytest.mark.gpu
+def test_emulated_fp64_spatiotemporal():
+    S = need_gpu()
+    M = W.spatiotemporal(nt=12, side=8, a=16, rho=0.9, tau=1.0, seed=0)
+    Lr, Sr, ldr = O.selinv(M)
+    L, Sg, ld, status = run_gpu(M, "fused", precision=S.STILES_EMU64)
+    assert status[0] == 0
+    assert rel_err(Sg, Sr) < EMU_TOL and abs(ld - ldr) < EMU_TOL * abs(ldr)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", PREC_SHAPES)
+def test_fp32_class_error_is_reported(shape):
+    """FP32-class products: the error against the FP64 oracle is reported
+    (printed) and must stay at FP32 level for these well-conditioned cases."""
+    S = need_gpu()
+    M = W.random_arrowhead(*shape, seed=sum(shape) + 2)
+    Lr, Sr, ldr = O.selinv(M)
+    L, Sg, ld, status = run_gpu(M, "fused", precision=S.STILES_FP32X)
+    assert status[0] == 0
+    err = rel_err(Sg, Sr)
+    print(f"FP32-class {shape}: Sigma rel err {err:.3e}, L rel err {rel_err(L, Lr):.3e}, logdet abs err {abs(ld - ldr):.3e}")
+    assert err < 1e-4
