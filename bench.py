@@ -118,6 +118,26 @@ def dist_init():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (the slowest rank's time): an
+    all-reduce MAX over the default process group, on the device its backend
+    uses (NCCL: the current CUDA device; gloo: host)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, units_per_step: float, t_max: float) -> float:
+    """Units processed by all ranks (each rank runs its own replica) per
+    second of the slowest rank: weak scaling, no data-path collective."""
+    return world * steps * units_per_step / t_max
+
+
 def oracle_sample(nt_sample: int):
     """Run the CPU oracle on the first nt_sample tile columns of the workload
     family; returns (seconds, flops)."""
@@ -250,11 +270,8 @@ def run_ours(args, world, rank, local):
     code, info, _ = st.status()
     if code != S.STILES_OK:
         raise SystemExit(f"timed launch failed: {S.strerror(code)}")
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = world * args.steps * flops / t_max / 1e12
+    t_max = max_over_ranks(t_local, world)
+    value = whole_job_rate(world, args.steps, flops, t_max) / 1e12
 
     # end to end through the public API with host buffers (H2D of A, D2H of Sigma)
     S_host = torch.empty(st.doubles if not args.no_e2e else 1, dtype=torch.float64).pin_memory()
@@ -269,10 +286,8 @@ def run_ours(args, world, rank, local):
             st.factor_selinv_host(A_host, S_host, stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        te = torch.tensor([e0.elapsed_time(e1) / 1e3], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = world * e2e_steps * flops / float(te.item()) / 1e12
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        e2e_value = whole_job_rate(world, e2e_steps, flops, te) / 1e12
 
     variants = None if args.no_variants else measure_variants(S, st, stream, dev, flops, logdet, args)
 
@@ -291,7 +306,7 @@ def run_ours(args, world, rank, local):
                        flops_per_step=flops, flop_convention="tile ops: POTRF/TRTRI/LAUUM m^3/3, TRSM/TRMM m k^2, "
                        "SYRK and symmetric Sigma_ii update m^2 k, GEMM 2mnk",
                        l2="inputs larger than L2 (A, L, Sigma 3.45 GB each; L2 129 MB)"),
-        "matrices_per_s": world * args.steps / t_max,
+        "matrices_per_s": whole_job_rate(world, args.steps, 1.0, t_max),
         "logdet": logdet,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_host.numel() * 8),

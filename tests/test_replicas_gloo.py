@@ -1,0 +1,55 @@
+"""The multi-GPU path is replicas only (one matrix does not shard; section
+"Multi-GPU" of the design): each rank factors its own copy and the bench
+reports all ranks' work over the slowest rank's time. This checks that host
+logic with two gloo ranks on the CPU (no GPU, no collective on the data path)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t_local = [1.5, 2.5][rank]  # the slower rank defines the job time
+        t_max = bench.max_over_ranks(t_local, world)
+        rate = bench.whole_job_rate(world, 4, 1.6e12, t_max)
+        out.put((rank, t_max, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_max_time_and_weak_scaling_rate():
+    mp = pytest.importorskip("torch.multiprocessing")
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, t_max, rate in res:
+        assert t_max == 2.5
+        assert rate == pytest.approx(2 * 4 * 1.6e12 / 2.5)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        steps, warmup, gpus = 1, 0, 2
+    bench.run_reference(A(), 2, 1)  # rank 1: no work, no output
+    assert capsys.readouterr().out == ""
