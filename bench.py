@@ -215,6 +215,152 @@ def measure_variants(S, st, stream, dev, flops, logdet64, args):
     return out
 
 
+BATCH = {"workload": "batched_uneven_arrowheads", "count": 64, "seed": 0, "nt": "U{20..200}",
+         "b": "{128, 256, 512}", "w": "U{1..4}", "a": "U{8..128}",
+         "values": "off-diagonal N(0,1)*0.1, diagonal 1 + full-row absolute sum (torch generator, seed 1000 + m)"}
+
+
+def used_mask(layouts, off, doubles, device):
+    """Boolean mask of the batch buffer entries that belong to a pattern tile
+    (padding and unused sub-diagonal slots are never written)."""
+    import torch
+    mask = torch.zeros(doubles, dtype=torch.bool, device=device)
+    for m, lay in enumerate(layouts):
+        for (i, k) in lay.pattern():
+            o = off[m] + lay.offset(i, k)
+            mask[o:o + lay.rows(i) * lay.rows(k)] = True
+    return mask
+
+
+def run_batched(args, world, rank, local):
+    """Config of many uneven matrices: one graph launch per batch, FP64 and
+    the reduced-precision modes, against plain FP64 per-matrix launches."""
+    import torch
+
+    from paper_2504_19171_gb300 import build as B
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    from paper_2504_19171_gb300 import autotune as AT
+    from paper_2504_19171_gb300 import stiles as S
+    from paper_2504_19171_gb300 import workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    shapes = W.batch_shapes(BATCH["count"], seed=BATCH["seed"])
+    count = len(shapes)
+    tuner = AT.Autotuner(AT.default_cache_path()) if not args.no_autotune else None
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    A = None
+    results, S64, mask = {}, None, None
+    clk = None
+    for name, prec in (("fp64", S.STILES_FP64), ("emu64", S.STILES_EMU64), ("fp32x", S.STILES_FP32X)):
+        if name != "fp64" and args.no_variants:
+            continue
+        tuning = tuner.codes_for(shapes, prec) if tuner else None
+        t_create = time.perf_counter()
+        bt = S.StilesBatch(shapes, device=str(dev), precision=prec, tuning=tuning, wait_budget_s=60)
+        t_create = time.perf_counter() - t_create
+        if A is None:
+            A = torch.empty(bt.doubles, dtype=torch.float64, device=dev)
+            for m, sh in enumerate(shapes):
+                W.random_arrowhead_packed(*sh, 1000 + m, A[bt.off[m]:bt.off[m] + bt.layouts[m].doubles])
+            mask = used_mask(bt.layouts, bt.off, bt.doubles, dev)
+        bt.A = A
+        flops = S.stiles_batch_stats(bt.h)["flops"]
+        for _ in range(args.warmup):
+            bt.factor_selinv(stream)
+        torch.cuda.synchronize(dev)
+        bad = [m for m in range(count) if bt.status(m)[0] != S.STILES_OK]
+        if bad:
+            raise SystemExit(f"batched {name}: matrices {bad} failed")
+        barrier()
+        sampler = ClockSampler(dev.index if dev.index is not None else 0).start() if name == "fp64" else None
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        for k in range(args.steps):
+            bt.factor_selinv(stream)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        if sampler:
+            clk = sampler.stop()
+        t_max = max_over_ranks(ev[0].elapsed_time(ev[-1]) / 1e3, world)
+        per_launch = ev[0].elapsed_time(ev[-1]) / 1e3 / args.steps
+        r = {"matrices_per_s": whole_job_rate(world, args.steps, count, t_max),
+             "value": whole_job_rate(world, args.steps, flops, t_max) / 1e12, "unit": "TFLOP/s",
+             "ms_per_batch": 1e3 * t_max / args.steps, "create_s": t_create,
+             "achieved_per_launch": flops / per_launch / 1e12, "flops_per_batch": flops,
+             "tuning": None if tuning is None else sorted(set(tuning))}
+        if name == "fp64":
+            S64 = bt.S.clone()
+        else:
+            d = (bt.S - S64).abs()
+            r["sigma_err_vs_fp64"] = max(float(d[bt.off[m]:bt.off[m] + bt.layouts[m].doubles][
+                mask[bt.off[m]:bt.off[m] + bt.layouts[m].doubles]].max() /
+                S64[bt.off[m]:bt.off[m] + bt.layouts[m].doubles][
+                mask[bt.off[m]:bt.off[m] + bt.layouts[m].doubles]].abs().max()) for m in range(count))
+        results[name] = r
+        bt.A = None
+        bt.close()
+        del bt
+        torch.cuda.empty_cache()
+    # plain FP64 per-matrix form: one handle and one launch per matrix, in sequence
+    off = [0]
+    for sh in shapes:
+        lay = S.PackedLayout(*sh)
+        off.append(off[-1] + -(-lay.doubles // 32) * 32)
+    t_solo, same = 0.0, 0
+    for m, sh in enumerate(shapes):
+        st = S.Stiles(*sh, device=str(dev))
+        st.A = A[off[m]:off[m] + st.doubles]
+        st.factor_selinv(stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.factor_selinv(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_solo += e0.elapsed_time(e1) / 1e3
+        mk = mask[off[m]:off[m] + st.doubles]
+        same += int(torch.equal(st.S[mk], S64[off[m]:off[m] + st.doubles][mk]))
+        st.A = None
+        st.close()
+    t_solo = max_over_ranks(t_solo, world)
+    fp = results["fp64"]
+    line = {
+        "metric": "batched factor+selinv matrices/s (FP64; EMU64 / FP32X variants; vs plain FP64 per-matrix)",
+        "value": fp["matrices_per_s"], "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": fp["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(BATCH, parallelism=f"replicas{world}" if world > 1 else "single",
+                       l2="inputs larger than L2 (26 GB of A per batch)", autotuned=tuner is not None),
+        "tflops": fp["value"], "clocks": clk,
+        "e2e": None,
+        "gpu_launches": args.steps * (1 + (0 if args.no_variants else 2)) + count,
+        "per_matrix_fp64": {"matrices_per_s": whole_job_rate(world, 1, count, t_solo), "seconds": t_solo,
+                            "bitwise_equal_to_batch": f"{same}/{count}"},
+        "variants": {k: v for k, v in results.items() if k != "fp64"},
+        "fp64": fp,
+        "roofline": {"bound": "alu", "achieved": fp["achieved_per_launch"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": fp["achieved_per_launch"] / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "stiles::persistent_kernel (FP64 pipe)"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -344,10 +490,15 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],
                     help="tile columns (default 200; smaller values are profiling cases, not bench lines)")
+    ap.add_argument("--workload", default="spatiotemporal", choices=["spatiotemporal", "batched"],
+                    help="spatiotemporal: the n = 204,864 matrix (default); batched: 64 uneven matrices per launch")
+    ap.add_argument("--no-autotune", action="store_true", help="batched: default tuning codes")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

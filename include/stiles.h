@@ -104,6 +104,20 @@ enum stiles_precision { STILES_FP64 = 0, STILES_EMU64 = 1, STILES_FP32X = 2 };
  * On success *out owns the handle; release it with stiles_destroy. */
 int stiles_create(int nt, int b, int band, int arrow, int precision, stiles_t *out);
 
+/* Same as stiles_create with a tuning code (0 = the defaults; the project's
+ * autotuner picks one per (b, band, arrow blocks, precision)). It changes
+ * only how the work is cut into tasks. Bits 2-5 split output blocks among
+ * CTAs differently (bit-identical results); bits 0-1 group the factor's
+ * update terms differently (results equal up to rounding):
+ *   bits 0-1  factor: source block columns per update task for tile columns
+ *             older than k-1 (0: 8, 1: 4, 2: 16, 3: 32)
+ *   bits 2-3  phase 2: parts of an off-diagonal Sigma block task
+ *             (0: four 32 x 32 quadrants, 1: two 32-row halves, 2: whole)
+ *   bits 4-5  factor: parts of the newest update of an off-diagonal block
+ *             (0: four quadrants, 1: whole)
+ * Other codes return STILES_ERR_INVALID_ARG. */
+int stiles_create_tuned(int nt, int b, int band, int arrow, int precision, int tuning, stiles_t *out);
+
 /* Doubles of one packed A / L / Sigma buffer (see the layout above). */
 int stiles_layout_doubles(stiles_t h, size_t *doubles);
 
@@ -214,7 +228,8 @@ int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size
 
 /* Plan statistics for a shape, computed on the host (no GPU, no handle).
  * which: 0 = factor plan, 1 = selinv plan, 2 = fused plan, plus 16 x the
- * stiles_precision of the plan (e.g. 2 + 16 * STILES_EMU64); workers = number
+ * stiles_precision of the plan (e.g. 2 + 16 * STILES_EMU64), plus 256 x a
+ * tuning code (stiles_create_tuned); workers = number
  * of persistent workers the list schedule assumes (e.g. the SM count).
  * stats[0] tasks, [1] segments, [2] waits, [3] counters,
  * [4] algorithmic flops of the tile operations (POTRF, TRTRI, LAUUM m^3/3;
@@ -251,6 +266,75 @@ int stiles_debug_break_plan(stiles_t h, int which);
 int stiles_destroy(stiles_t h);
 
 /* Human-readable name of a status code. */
+/* ---------------------------------------------------------------- batch --
+ * Many independent matrices of different shapes factored and inverted in ONE
+ * persistent launch (no counterpart in the paper, which treats one matrix at
+ * a time). Their task tables are merged into one table and ordered by one
+ * critical-path list schedule, so the small matrices fill the GPU beside the
+ * sequential factorization chains of the large ones.
+ *
+ * Layout. Matrix m occupies doubles [off[m], off[m] + stiles_layout_doubles
+ * of its shape) of each batch buffer (A, L, Sigma), in the packed band+arrow
+ * layout of its own shape; off[] (multiples of 32 doubles) comes from
+ * stiles_batch_offsets. A, L and Sigma are separate caller buffers of
+ * off[count] doubles each (A may alias L); the scratch buffer holds every
+ * matrix's L^-1 / U tiles at the same offsets plus the scheduler state.
+ *
+ * Launch. stiles_batch_factor_selinv enqueues a CUDA graph (built on the first
+ * call for a given set of buffer pointers, re-used while they stay the same)
+ * whose nodes reset the scheduler state and the status blocks and run the
+ * persistent kernel: one graph launch per batch. Asynchronous; one launch at
+ * a time per batch handle.
+ *
+ * Status. Per matrix: STILES_OK, STILES_ERR_NOT_SPD with the 1-based global
+ * column of its first failing pivot, or the launch-wide STILES_ERR_TIMEOUT /
+ * STILES_ERR_PLAN (a timeout stops every matrix). */
+typedef struct stiles_batch *stiles_batch_t;
+
+/* count >= 1 shapes (nt[m], b[m], band[m], arrow[m], as for stiles_create),
+ * one precision for the whole batch, tuning[m] as for stiles_create_tuned
+ * (NULL: all 0). Returns the codes of stiles_create. */
+int stiles_batch_create(int count, const int *nt, const int *b, const int *band, const int *arrow, int precision,
+                        const int *tuning, stiles_batch_t *out);
+
+/* off[0 .. count]: offset (doubles) of each matrix in the batch buffers;
+ * off[count] = doubles of each of the A, L and Sigma buffers. */
+int stiles_batch_offsets(stiles_batch_t h, size_t *off);
+
+/* Bytes of each of A, L, Sigma (off[count] doubles) and of the scratch. */
+int stiles_batch_workspace_bytes(stiles_batch_t h, size_t *buffer_bytes, size_t *scratch_bytes);
+
+/* Fused factor + selected inversion of every matrix of the batch in one graph
+ * launch on `stream` (a cudaStream_t, or NULL for the default stream).
+ * scratch must be 256-byte aligned. */
+int stiles_batch_factor_selinv(stiles_batch_t h, const double *A, double *L, double *Sigma, void *scratch,
+                               void *stream);
+
+/* Status of matrix `index` after the last launch (waits for it): *code as
+ * above, *info = 1-based failing column for NOT_SPD, else 0. */
+int stiles_batch_status(stiles_batch_t h, int index, int *code, long long *info);
+
+/* logdet of every matrix (out_host[count]); waits for the last launch.
+ * Entries of matrices whose status is not STILES_OK are NaN. Returns the
+ * launch-wide error (TIMEOUT / PLAN) if there was one, else STILES_OK. */
+int stiles_batch_logdet(stiles_batch_t h, double *out_host);
+
+/* STILES_OPT_WAIT_BUDGET_NS and STILES_OPT_GRID, as for a single handle. */
+int stiles_batch_set_option(stiles_batch_t h, int option, long long value);
+
+/* Plan statistics of the merged table (same fields as stiles_plan_stats). */
+int stiles_batch_stats(stiles_batch_t h, long long stats[8]);
+
+/* Test hook (host only, no device): build the merged table of a batch and
+ * emulate a launch of it (bounds of every access within the batch buffers,
+ * queue capacities, every task released once). Returns STILES_OK or
+ * STILES_ERR_PLAN. */
+int stiles_debug_validate_batch(int count, const int *nt, const int *b, const int *band, const int *arrow,
+                                int precision, const int *tuning);
+
+/* Waits for the last launch, frees the tables, the graph and the handle. */
+int stiles_batch_destroy(stiles_batch_t h);
+
 const char *stiles_strerror(int code);
 
 #ifdef __cplusplus

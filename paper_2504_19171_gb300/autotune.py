@@ -1,0 +1,101 @@
+"""Autotuner of the plan tuning code (``stiles_create_tuned`` /
+``stiles_batch_create``).
+
+The planner cuts the work into tasks in several legal ways (tuning code bit
+fields, see include/stiles.h): how many source block columns one factor
+update task applies, and into how many CTA parts phase-2 and factor update
+blocks are split. Which cut is fastest depends on the tile order b, the
+bandwidth w, the number of arrow block rows and the precision, so the tuner
+times the candidate codes on a probe batch of that key (several copies of a
+short matrix of the same b, w, a, run in one launch so that the GPU is as
+loaded as in a real batch) and keeps the fastest. Results are cached in a
+JSON file, keyed ``b:w:arrow_blocks:precision``.
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Iterable, Optional, Tuple
+
+from . import stiles as S
+from . import workloads as W
+
+# chunk of old update terms (bits 0-1) x phase-2 split (bits 2-3) x newest-update split (bits 4-5)
+CANDIDATES = (0, 1, 2, 4, 8, 16, 4 + 16, 2 + 8 + 16)
+FB = 64
+
+
+def default_cache_path() -> str:
+    """The tuning file shipped with the package (codes measured on GB300),
+    used as the starting cache; keys it lacks are tuned and added."""
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+
+
+def key_of(b: int, w: int, a: int, precision: int) -> str:
+    return f"{b}:{w}:{(a + FB - 1) // FB}:{precision}"
+
+
+class Autotuner:
+    def __init__(self, cache_path: Optional[str] = None, nt_probe: int = 12, copies: int = 8, reps: int = 2,
+                 candidates: Iterable[int] = CANDIDATES, device: str = "cuda"):
+        self.cache_path = cache_path
+        self.nt_probe, self.copies, self.reps = nt_probe, copies, reps
+        self.candidates = tuple(candidates)
+        self.device = device
+        self.cache: Dict[str, dict] = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                self.cache = json.load(f)
+
+    def save(self) -> None:
+        if self.cache_path:
+            tmp = self.cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.cache_path)
+
+    def best(self, b: int, w: int, a: int, precision: int = S.STILES_FP64) -> int:
+        k = key_of(b, w, a, precision)
+        if k not in self.cache:
+            code, times = self.tune(b, w, a, precision)
+            self.cache[k] = {"code": code, "seconds": {str(c): t for c, t in times.items()}}
+            self.save()
+        return int(self.cache[k]["code"])
+
+    def codes_for(self, shapes, precision: int = S.STILES_FP64):
+        return [self.best(b, w, a, precision) for (_, b, w, a) in shapes]
+
+    def tune(self, b: int, w: int, a: int, precision: int) -> Tuple[int, Dict[int, float]]:
+        """Time every candidate code on the probe batch; returns (best code,
+        {code: seconds per launch})."""
+        import torch
+
+        nt = max(self.nt_probe, w + 1)
+        shapes = [(nt, b, w, a)] * self.copies
+        A = None
+        times: Dict[int, float] = {}
+        for code in self.candidates:
+            bt = S.StilesBatch(shapes, device=self.device, precision=precision, tuning=[code] * self.copies)
+            try:
+                if A is None:
+                    A = torch.empty(bt.doubles, dtype=torch.float64, device=bt.device)
+                    for m in range(self.copies):
+                        lay = bt.layouts[m]
+                        W.random_arrowhead_packed(nt, b, w, a, 500 + m, A[bt.off[m]:bt.off[m] + lay.doubles])
+                bt.A = A
+                bt.factor_selinv()  # warm-up (and the graph build)
+                torch.cuda.synchronize(bt.device)
+                if any(bt.status(m)[0] != S.STILES_OK for m in range(self.copies)):
+                    raise RuntimeError(f"autotune probe failed for code {code}")
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(self.reps):
+                    bt.factor_selinv()
+                e1.record()
+                torch.cuda.synchronize(bt.device)
+                times[code] = e0.elapsed_time(e1) / 1e3 / self.reps
+            finally:
+                bt.A = None
+                bt.close()
+        best = min(times, key=times.get)
+        return best, times

@@ -108,6 +108,13 @@ struct Builder {
     else if (mode == PM_TRI3 && t.m > 32 && t.m == t.n) { t.pmode = PM_TRI3; t.parts = 3; }
   }
 
+  // Parts of an off-diagonal phase-2 block task (tuning bits 2-3).
+  void split_p2(Task& t) const {
+    const int mode = tune_p2_split(s.tune);
+    if (mode == 0) split(t, PM_QUAD4);
+    else if (mode == 1) split(t, PM_ROWS2);
+  }
+
   // Mark a bulk product task with the plan's reduced precision. The emulated
   // FP64 kernel works on sub-tiles of at most 32 x 32: blocks that are not
   // already split that way run as a grid of such tiles.
@@ -239,7 +246,7 @@ struct Builder {
     // block is due: batch them (kChunkOld block columns per task). Updates from
     // tile column kq-1 and from kq itself arrive one block column at a time
     // along the critical path: one block column per task.
-    const int kChunkOld = 8;
+    const int kChunkOld = tune_chunk_old(s.tune);
     for (int k : ks) {
       const int step = (k < kq - 1) ? kChunkOld : 1;
       for (int c0 = 0; c0 < L.nblk(k); c0 += step) terms.push_back({k, c0, std::min(L.nblk(k), c0 + step) - 1});
@@ -271,7 +278,7 @@ struct Builder {
       // a diagonal block only needs its lower quadrants; the newest update of
       // a block gates its TRSM / POTRF on the critical path: split it 4 ways
       if (diag) split(tk, PM_TRI3);
-      else if (t + 1 == nchain) split(tk, PM_QUAD4);
+      else if (t + 1 == nchain && tune_upd_split(s.tune) == 0) split(tk, PM_QUAD4);
       if (grow(i, r) - grow(terms[t].k, terms[t].c1) <= kUrgentReach) tk.flags |= TF_URGENT;
       lower_precision(tk);
       std::vector<Wait> w;
@@ -445,7 +452,7 @@ struct Builder {
         for (int r = 0; r < L.nblk(j); ++r) {
           const int m = L.bdim(j, r), n = L.bdim(i, c);
           Task t = blank(OP_NEG, m, n);
-          split(t, PM_QUAD4);  // phase 2 is a chain of joins: shorter tasks, shorter steps
+          split_p2(t);  // phase 2 is a chain of joins: shorter tasks, shorter steps
           t.out = mkref(BUF_S, L.blk(j, i, r, c));
           t.ldo = ldj;
           std::vector<Seg> segs;
@@ -478,7 +485,8 @@ struct Builder {
       for (int c = 0; c <= r; ++c) {
         const int m = L.bdim(i, r), n = L.bdim(i, c);
         Task t = blank(OP_SYMUPD, m, n);
-        split(t, r == c ? PM_TRI3 : PM_QUAD4);
+        if (r == c) split(t, PM_TRI3);
+        else split_p2(t);
         t.out = mkref(BUF_S, L.blk(i, i, r, c));
         t.ldo = ld;
         t.cin = t.out;
@@ -672,18 +680,76 @@ double tile_flops(const Shape& s, PlanKind kind) {
   return f;
 }
 
-int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out) {
-  if (s.nt < 1 || s.b < 1 || s.w < 0 || s.a < 0 || s.w > s.nt - 1) return STILES_ERR_INVALID_ARG;
-  // Task-table size guard: about (1+w+1) tiles per column, nblk^2 blocks per
-  // tile and up to (w+1)*nblk + nblk chain tasks per block.
+// Task-table size estimate: about (1+w+1) tiles per column, nblk^2 blocks per
+// tile and up to (w+1)*nblk + nblk chain tasks per block.
+static double task_estimate(const Shape& s) {
   const double nb = (s.b + FB - 1) / FB, na = (s.a + FB - 1) / FB;
-  const double est = (double)s.nt * (s.w + 2) * nb * (nb + na) * ((s.w + 2) * nb + 8);
-  if (est > 4.0e8) return STILES_ERR_INVALID_ARG;
+  return (double)s.nt * (s.w + 2) * nb * (nb + na) * ((s.w + 2) * nb + 8);
+}
+
+static bool shape_ok(const Shape& s) {
+  return s.nt >= 1 && s.b >= 1 && s.w >= 0 && s.a >= 0 && s.w <= s.nt - 1 && tune_valid(s.tune);
+}
+
+int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out) {
+  if (!shape_ok(s)) return STILES_ERR_INVALID_ARG;
+  if (task_estimate(s) > 4.0e8) return STILES_ERR_INVALID_ARG;
   Builder B(s, kind, out);
   if (kind == PLAN_FACTOR || kind == PLAN_FUSED) B.build_factor();
   if (kind == PLAN_SELINV || kind == PLAN_FUSED) B.build_selinv();
   B.flops = tile_flops(s, kind);
   int rc = B.finish(workers);
+  if (rc) return rc;
+  return check_plan(*out);
+}
+
+int build_batch_plan(const std::vector<Shape>& shapes, const std::vector<int64_t>& base, int workers, Plan* out,
+                     std::vector<int32_t>* diag_base) {
+  if (shapes.empty() || base.size() != shapes.size() || !out || !diag_base) return STILES_ERR_INVALID_ARG;
+  double est = 0;
+  for (const Shape& s : shapes) {
+    if (!shape_ok(s) || s.prec != shapes[0].prec) return STILES_ERR_INVALID_ARG;
+    est += task_estimate(s);
+  }
+  if (est > 4.0e8) return STILES_ERR_INVALID_ARG;
+  Builder M(shapes[0], PLAN_FUSED, out);
+  diag_base->assign(shapes.size() + 1, 0);
+  for (size_t m = 0; m < shapes.size(); ++m) {
+    Builder B(shapes[m], PLAN_FUSED, nullptr);
+    B.build_factor();
+    B.build_selinv();
+    const int32_t toff = (int32_t)M.tasks.size(), coff = (int32_t)M.chain.size(), doff = M.ndiag;
+    const int64_t off = base[m];
+    auto shift = [off](int64_t ref) { return ref < 0 ? ref : ref + off; };
+    for (size_t t = 0; t < B.tasks.size(); ++t) {
+      Task tk = B.tasks[t];
+      tk.out = shift(tk.out);
+      tk.cin = shift(tk.cin);
+      tk.aux = shift(tk.aux);
+      if (tk.diag >= 0) tk.diag += doff;
+      M.tasks.push_back(tk);
+      M.cost.push_back(B.cost[t]);
+      for (Seg& g : B.tsegs[t]) {
+        g.a = shift(g.a);
+        g.b = shift(g.b);
+      }
+      M.tsegs.push_back(std::move(B.tsegs[t]));
+      for (Wait& w : B.twaits[t]) w.ctr += coff;
+      M.twaits.push_back(std::move(B.twaits[t]));
+      for (int32_t& c : B.tsigs[t]) c += coff;
+      M.tsigs.push_back(std::move(B.tsigs[t]));
+    }
+    for (size_t c = 0; c < B.chain.size(); ++c) {
+      M.chain.push_back(B.chain[c]);
+      for (int32_t& id : B.writers[c]) id += toff;
+      M.writers.push_back(std::move(B.writers[c]));
+    }
+    M.ndiag += B.ndiag;
+    M.tile_gemms += B.tile_gemms;
+    M.flops += tile_flops(shapes[m], PLAN_FUSED);
+    (*diag_base)[m + 1] = M.ndiag;
+  }
+  const int rc = M.finish(workers);
   if (rc) return rc;
   return check_plan(*out);
 }
@@ -721,11 +787,11 @@ namespace stiles {
 // queue slot index stays inside its bucket or the urgent queue, and the
 // successor graph releases every task exactly once. Returns 0 or
 // STILES_ERR_PLAN (and prints the first problem to stderr).
-int validate_plan(const Plan& p, const Shape& s, int kind) {
+int validate_plan(const Plan& p, const Shape& s, int kind) { return validate_plan_len(p, Layout(s).doubles(), kind); }
+
+int validate_plan_len(const Plan& p, int64_t lim, int kind) {
   // buffers a launch of this kind provides: factor A, L, scratch; selinv L, Sigma, scratch
   const unsigned allowed = kind == PLAN_FACTOR ? 0xBu : kind == PLAN_SELINV ? 0xEu : 0xFu;
-  const Layout L(s);
-  const int64_t lim = L.doubles();
   const int nt = (int)p.tasks.size();
   auto bad = [&](const char* what, int t) {
     fprintf(stderr, "validate_plan: %s (task %d, op %d)\n", what, t, t >= 0 ? (int)p.tasks[t].op : -1);

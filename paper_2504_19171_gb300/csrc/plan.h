@@ -104,9 +104,26 @@ namespace stiles {
 
 enum PlanKind : int { PLAN_FACTOR = 0, PLAN_SELINV = 1, PLAN_FUSED = 2 };
 
+// Tuning code of a plan (bit fields; 0 = the defaults). It changes how work is
+// cut into tasks, never what is computed: bits 2-5 only re-partition output
+// blocks among CTAs (bit-identical results), bits 0-1 regroup the factor's
+// update terms (the same sums, rounded at other points).
+//   bits 0-1  factor: source block columns per update task for tile columns
+//             older than k-1 (0: 8, 1: 4, 2: 16, 3: 32)
+//   bits 2-3  phase 2: parts of an off-diagonal Sigma block task
+//             (0: four 32 x 32 quadrants, 1: two 32-row halves, 2: whole block)
+//   bits 4-5  factor: parts of the newest update of an off-diagonal block
+//             (0: four quadrants, 1: whole block)
+enum : int { kTuneBits = 6 };
+inline int tune_chunk_old(int t) { const int v[4] = {8, 4, 16, 32}; return v[t & 3]; }
+inline int tune_p2_split(int t) { return (t >> 2) & 3; }
+inline int tune_upd_split(int t) { return (t >> 4) & 3; }
+inline bool tune_valid(int t) { return t >= 0 && t < (1 << kTuneBits) && tune_p2_split(t) <= 2 && tune_upd_split(t) <= 1; }
+
 struct Shape {
   int nt, b, w, a;  // w already clipped to nt-1
   int prec = PREC_FP64;  // precision of the off-diagonal bulk products (Precision)
+  int tune = 0;          // tuning code (see above)
 };
 
 // Dynamic schedule: a task becomes ready when its last predecessor finishes
@@ -179,6 +196,19 @@ int check_plan(const Plan& p);
 // Host emulation of a launch of the plan (bounds of every access, queue
 // capacities, every task released once). Returns 0 or STILES_ERR_PLAN.
 int validate_plan(const Plan& p, const Shape& s, int kind);
+// The same with an explicit buffer length (doubles in each of A, L, Sigma and
+// the scratch's packed part), for batch plans.
+int validate_plan_len(const Plan& p, int64_t buf_doubles, int kind);
+
+// One fused (factor + selected inversion) task table for a batch of
+// independent matrices: matrix m's tiles live at offset base[m] (doubles) of
+// each of the shared A, L, Sigma and scratch buffers; its tasks, counters and
+// logdet slots are renumbered into one table and ordered by one list
+// schedule over all of them, so the small matrices fill the GPU beside the
+// critical paths of the large ones. diag_base[m] .. diag_base[m+1] are the
+// logdet / pivot slots of matrix m. Returns 0 or a negative status code.
+int build_batch_plan(const std::vector<Shape>& shapes, const std::vector<int64_t>& base, int workers, Plan* out,
+                     std::vector<int32_t>* diag_base);
 
 }  // namespace stiles
 #endif

@@ -105,13 +105,17 @@ static void free_handle(stiles_handle* h) {
 }
 
 extern "C" int stiles_create(int nt, int b, int band, int arrow, int precision, stiles_t* out) {
+  return stiles_create_tuned(nt, b, band, arrow, precision, 0, out);
+}
+
+extern "C" int stiles_create_tuned(int nt, int b, int band, int arrow, int precision, int tuning, stiles_t* out) {
   if (!out) return STILES_ERR_INVALID_ARG;
   *out = nullptr;
-  if (nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
+  if (nt < 1 || b < 1 || band < 0 || arrow < 0 || !tune_valid(tuning)) return STILES_ERR_INVALID_ARG;
   if (precision != STILES_FP64 && precision != STILES_EMU64 && precision != STILES_FP32X) return STILES_ERR_UNSUPPORTED;
   stiles_handle* h = new (std::nothrow) stiles_handle();
   if (!h) return STILES_ERR_OOM;
-  h->s = Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision};
+  h->s = Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision, tuning};
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;
@@ -363,11 +367,12 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
 }
 
 extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]) {
-  const int kind = which & 15, prec = which >> 4;
-  if (!stats || kind < 0 || kind > 2 || prec < 0 || prec > PREC_FP32X || workers < 1) return STILES_ERR_INVALID_ARG;
+  const int kind = which & 15, prec = (which >> 4) & 15, tune = which >> 8;
+  if (!stats || kind < 0 || kind > 2 || prec > PREC_FP32X || workers < 1 || !tune_valid(tune))
+    return STILES_ERR_INVALID_ARG;
   if (nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
   Plan p;
-  int rc = build_plan(Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec}, (PlanKind)kind, workers, &p);
+  int rc = build_plan(Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune}, (PlanKind)kind, workers, &p);
   if (rc) return rc;
   stats[0] = (long long)p.tasks.size();
   stats[1] = (long long)p.segs.size();
@@ -381,10 +386,10 @@ extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, 
 }
 
 extern "C" int stiles_debug_validate(int nt, int b, int band, int arrow, int which) {
-  const int kind = which & 15, prec = which >> 4;
-  if (kind < 0 || kind > 2 || prec < 0 || prec > PREC_FP32X || nt < 1 || b < 1 || band < 0 || arrow < 0)
+  const int kind = which & 15, prec = (which >> 4) & 15, tune = which >> 8;
+  if (kind < 0 || kind > 2 || prec > PREC_FP32X || !tune_valid(tune) || nt < 1 || b < 1 || band < 0 || arrow < 0)
     return STILES_ERR_INVALID_ARG;
-  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec};
+  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune};
   Plan p;
   int rc = build_plan(sh, (PlanKind)kind, 304, &p);
   return rc ? rc : validate_plan(p, sh, kind);
@@ -467,4 +472,374 @@ extern "C" const char* stiles_strerror(int code) {
     case STILES_ERR_TOO_LARGE: return "shape too large for the fixed no-allocation scratch";
     default: return "unknown status";
   }
+}
+
+// ------------------------------------------------------------------ batch --
+
+struct stiles_batch {
+  int count = 0;
+  int device = 0;
+  int sms = 0;
+  int grid = 0;
+  int prec = 0;
+  long long budget_ns = 60LL * 1000 * 1000 * 1000;
+  std::vector<Shape> shapes;
+  std::vector<int64_t> off;        // count + 1 offsets (doubles)
+  std::vector<int32_t> diag_base;  // count + 1 POTRF slot ranges
+  std::vector<int64_t> slot_gcol;  // per POTRF slot: global column of its block's first pivot
+  Plan plan;
+  DevPlan dev;
+  DevStatus* dstatus = nullptr;
+  double* dlogdet = nullptr;
+  int32_t* dbad = nullptr;
+  int ndiag = 0;
+  size_t w_bytes = 0, ctr_offset = 0, scratch_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  bool launched = false;
+  // graph of one launch, valid for the buffer pointers it was built with
+  KParams kp{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[6] = {};
+};
+
+static void free_batch(stiles_batch* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  cudaFree(h->dev.tasks);
+  cudaFree(h->dev.segs);
+  cudaFree(h->dev.succ_off);
+  cudaFree(h->dev.succ);
+  cudaFree(h->dev.bcap);
+  cudaFree(h->dev.image);
+  cudaFree(h->dstatus);
+  cudaFree(h->dlogdet);
+  cudaFree(h->dbad);
+  delete h;
+}
+
+extern "C" int stiles_batch_create(int count, const int* nt, const int* b, const int* band, const int* arrow,
+                                   int precision, const int* tuning, stiles_batch_t* out) {
+  if (!out) return STILES_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || !nt || !b || !band || !arrow) return STILES_ERR_INVALID_ARG;
+  if (precision != STILES_FP64 && precision != STILES_EMU64 && precision != STILES_FP32X) return STILES_ERR_UNSUPPORTED;
+  stiles_batch* h = new (std::nothrow) stiles_batch();
+  if (!h) return STILES_ERR_OOM;
+  h->count = count;
+  h->prec = precision;
+  h->off.assign(count + 1, 0);
+  for (int m = 0; m < count; ++m) {
+    const int tune = tuning ? tuning[m] : 0;
+    if (nt[m] < 1 || b[m] < 1 || band[m] < 0 || arrow[m] < 0 || !tune_valid(tune)) {
+      delete h;
+      return STILES_ERR_INVALID_ARG;
+    }
+    const Shape s{nt[m], b[m], band[m] < nt[m] - 1 ? band[m] : nt[m] - 1, arrow[m], precision, tune};
+    h->shapes.push_back(s);
+    h->off[m + 1] = (int64_t)align_up((size_t)(h->off[m] + Layout(s).doubles()), 32);
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    delete h;
+    return STILES_ERR_CUDA;
+  }
+  h->grid = h->sms * kCtasPerSm;
+  std::vector<int64_t> base(h->off.begin(), h->off.end() - 1);
+  int rc = build_batch_plan(h->shapes, base, h->grid, &h->plan, &h->diag_base);
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  Plan& p = h->plan;
+  rc = upload(p.tasks, &h->dev.tasks);
+  if (!rc) rc = upload(p.segs, &h->dev.segs);
+  if (!rc) rc = upload(p.succ_off, &h->dev.succ_off);
+  if (!rc) rc = upload(p.succ, &h->dev.succ);
+  if (!rc) rc = upload(p.bcap, &h->dev.bcap);
+  {
+    std::vector<int32_t> img = sched_image(p);
+    if (!rc) rc = upload(img, &h->dev.image);
+    h->dev.image_ints = img.size();
+  }
+  h->dev.ntasks = (int)p.tasks.size();
+  h->dev.nbuckets = p.nbuckets;
+  h->dev.ucap = p.urgent_parts;
+  h->ndiag = p.ndiag;
+  if (!rc && cudaMalloc((void**)&h->dstatus, sizeof(DevStatus)) != cudaSuccess) rc = STILES_ERR_OOM;
+  if (!rc && cudaMalloc((void**)&h->dlogdet, sizeof(double) * (h->ndiag > 0 ? h->ndiag : 1)) != cudaSuccess)
+    rc = STILES_ERR_OOM;
+  if (!rc && cudaMalloc((void**)&h->dbad, sizeof(int32_t) * (h->ndiag > 0 ? h->ndiag : 1)) != cudaSuccess)
+    rc = STILES_ERR_OOM;
+  if (!rc && configure_persistent() != cudaSuccess) rc = STILES_ERR_CUDA;
+  if (rc) {
+    free_batch(h);
+    return rc;
+  }
+  h->slot_gcol.assign(h->ndiag, 0);
+  for (const Task& tk : p.tasks)
+    if (tk.op == OP_POTRF && tk.diag >= 0 && tk.diag < h->ndiag) h->slot_gcol[tk.diag] = tk.gcol;
+  // the task table is on the device; keep only what the host reads later
+  p.tasks.clear(); p.tasks.shrink_to_fit();
+  p.segs.clear(); p.segs.shrink_to_fit();
+  p.waits.clear(); p.waits.shrink_to_fit();
+  p.sigs.clear(); p.sigs.shrink_to_fit();
+  p.succ.clear(); p.succ.shrink_to_fit();
+  p.succ_off.clear(); p.succ_off.shrink_to_fit();
+  p.slots0.clear(); p.slots0.shrink_to_fit();
+  h->w_bytes = align_up((size_t)h->off[count] * sizeof(double), 256);
+  h->ctr_offset = h->w_bytes;
+  h->scratch_bytes = align_up(h->ctr_offset + sizeof(int) * h->dev.image_ints, 256);
+  *out = h;
+  return STILES_OK;
+}
+
+extern "C" int stiles_batch_offsets(stiles_batch_t h, size_t* off) {
+  if (!h || !off) return STILES_ERR_INVALID_ARG;
+  for (int m = 0; m <= h->count; ++m) off[m] = (size_t)h->off[m];
+  return STILES_OK;
+}
+
+extern "C" int stiles_batch_workspace_bytes(stiles_batch_t h, size_t* buffer_bytes, size_t* scratch_bytes) {
+  if (!h) return STILES_ERR_INVALID_ARG;
+  if (buffer_bytes) *buffer_bytes = (size_t)h->off[h->count] * sizeof(double);
+  if (scratch_bytes) *scratch_bytes = h->scratch_bytes;
+  return STILES_OK;
+}
+
+// Graph of one batch launch: reset the scheduler state (copy of the initial
+// image), the status block (zero, then "no failing column") and the pivot
+// slots (-1), then the persistent kernel.
+static int build_batch_graph(stiles_batch* h, const double* A, double* L, double* S, void* scratch) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  char* scr = (char*)scratch;
+  int* state = (int*)(scr + h->ctr_offset);
+  KParams& p = h->kp;
+  p = KParams{};
+  p.tasks = h->dev.tasks;
+  p.segs = h->dev.segs;
+  p.succ_off = h->dev.succ_off;
+  p.succ = h->dev.succ;
+  p.bcap = h->dev.bcap;
+  p.ntasks = h->dev.ntasks;
+  p.nbuckets = h->dev.nbuckets;
+  p.ucap = h->dev.ucap;
+  p.q = sched_state_at(state, h->dev.ntasks, h->dev.nbuckets, h->dev.ucap);
+  p.st = h->dstatus;
+  p.logdet_part = h->dlogdet;
+  p.badpiv = h->dbad;
+  p.buf[BUF_A] = const_cast<double*>(A);
+  p.buf[BUF_L] = L;
+  p.buf[BUF_S] = S;
+  p.buf[BUF_W] = (double*)scr;
+  p.budget_ns = h->budget_ns;
+  p.trace = nullptr;
+  p.buf_len = h->off[h->count];
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return STILES_ERR_CUDA;
+  std::vector<cudaGraphNode_t> deps;
+  cudaGraphNode_t n = nullptr;
+  bool ok = true;
+  if (h->dev.image_ints) {
+    ok = ok && cudaGraphAddMemcpyNode1D(&n, g, nullptr, 0, state, h->dev.image, sizeof(int) * h->dev.image_ints,
+                                        cudaMemcpyDeviceToDevice) == cudaSuccess;
+    deps.push_back(n);
+  }
+  cudaMemsetParams ms{};
+  ms.dst = h->dstatus;
+  ms.value = 0;
+  ms.elementSize = 4;
+  ms.width = sizeof(DevStatus) / 4;
+  ms.height = 1;
+  cudaGraphNode_t n_status = nullptr;
+  ok = ok && cudaGraphAddMemsetNode(&n_status, g, nullptr, 0, &ms) == cudaSuccess;
+  cudaMemsetParams ms2{};
+  ms2.dst = &h->dstatus->spd_col;
+  ms2.value = 0xffffffffu;
+  ms2.elementSize = 4;
+  ms2.width = sizeof(unsigned long long) / 4;
+  ms2.height = 1;
+  ok = ok && cudaGraphAddMemsetNode(&n, g, &n_status, 1, &ms2) == cudaSuccess;
+  deps.push_back(n);
+  if (h->ndiag > 0) {
+    cudaMemsetParams ms3{};
+    ms3.dst = h->dbad;
+    ms3.value = 0xffffffffu;
+    ms3.elementSize = 4;
+    ms3.width = (size_t)h->ndiag;
+    ms3.height = 1;
+    ok = ok && cudaGraphAddMemsetNode(&n, g, nullptr, 0, &ms3) == cudaSuccess;
+    deps.push_back(n);
+  }
+  if (h->dev.ntasks > 0) {
+    void* args[1] = {&h->kp};
+    cudaKernelNodeParams kn{};
+    kn.func = const_cast<void*>(persistent_kernel_ptr());
+    kn.gridDim = dim3((unsigned)h->grid);
+    kn.blockDim = dim3((unsigned)kernel_threads());
+    kn.sharedMemBytes = (unsigned)kernel_smem_bytes();
+    kn.kernelParams = args;
+    ok = ok && cudaGraphAddKernelNode(&n, g, deps.data(), deps.size(), &kn) == cudaSuccess;
+  }
+  cudaGraphExec_t ex = nullptr;
+  ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (!ok) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(g);
+    return STILES_ERR_CUDA;
+  }
+  h->graph = g;
+  h->gexec = ex;
+  return STILES_OK;
+}
+
+extern "C" int stiles_batch_factor_selinv(stiles_batch_t h, const double* A, double* L, double* S, void* scratch,
+                                          void* stream) {
+  if (!h || !A || !L || !S || !scratch || S == L || (const double*)S == A || (void*)S == scratch)
+    return STILES_ERR_INVALID_ARG;
+  if (((uintptr_t)scratch) % 256 != 0) return STILES_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
+  const void* key[6] = {A, L, S, scratch, (const void*)(intptr_t)h->grid, (const void*)(intptr_t)h->budget_ns};
+  if (!h->gexec || memcmp(key, h->gkey, sizeof(key)) != 0) {
+    const int rc = build_batch_graph(h, A, L, S, scratch);
+    if (rc) return rc;
+    memcpy(h->gkey, key, sizeof(key));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaGraphLaunch(h->gexec, st) != cudaSuccess) return STILES_ERR_CUDA;
+  h->last_stream = st;
+  h->launched = true;
+  return STILES_OK;
+}
+
+static int batch_sync(stiles_batch_t h, DevStatus* ds) {
+  if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return STILES_ERR_CUDA;
+  if (cudaMemcpy(ds, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost) != cudaSuccess) return STILES_ERR_CUDA;
+  return STILES_OK;
+}
+
+// First failing global column (0-based) of matrix m, or -1.
+static long long batch_bad_column(stiles_batch_t h, const std::vector<int32_t>& bad, int m) {
+  long long best = -1;
+  for (int q = h->diag_base[m]; q < h->diag_base[m + 1]; ++q)
+    if (bad[q] >= 0) {
+      const long long col = h->slot_gcol[q] + bad[q];
+      if (best < 0 || col < best) best = col;
+    }
+  return best;
+}
+
+extern "C" int stiles_batch_status(stiles_batch_t h, int index, int* code, long long* info) {
+  if (!h || index < 0 || index >= h->count) return STILES_ERR_INVALID_ARG;
+  if (!h->launched) {
+    if (code) *code = STILES_OK;
+    if (info) *info = 0;
+    return STILES_OK;
+  }
+  DevStatus ds;
+  int rc = batch_sync(h, &ds);
+  if (rc) return rc;
+  int c = code_of(ds);
+  long long inf = c == STILES_OK || c == STILES_ERR_NOT_SPD ? 0 : (long long)ds.info;
+  if (c == STILES_OK || c == STILES_ERR_NOT_SPD) {
+    const int n = h->diag_base[index + 1] - h->diag_base[index];
+    std::vector<int32_t> bad(h->ndiag, -1);
+    if (n > 0 && cudaMemcpy(bad.data() + h->diag_base[index], h->dbad + h->diag_base[index], sizeof(int32_t) * n,
+                            cudaMemcpyDeviceToHost) != cudaSuccess)
+      return STILES_ERR_CUDA;
+    const long long col = batch_bad_column(h, bad, index);
+    c = col >= 0 ? STILES_ERR_NOT_SPD : STILES_OK;
+    inf = col >= 0 ? col + 1 : 0;
+  }
+  if (code) *code = c;
+  if (info) *info = inf;
+  return STILES_OK;
+}
+
+extern "C" int stiles_batch_logdet(stiles_batch_t h, double* out_host) {
+  if (!h || !out_host || !h->launched) return STILES_ERR_INVALID_ARG;
+  DevStatus ds;
+  int rc = batch_sync(h, &ds);
+  if (rc) return rc;
+  const int c = code_of(ds);
+  if (c != STILES_OK && c != STILES_ERR_NOT_SPD) return c;
+  std::vector<double> part(h->ndiag > 0 ? h->ndiag : 1);
+  std::vector<int32_t> bad(h->ndiag > 0 ? h->ndiag : 1, -1);
+  if (h->ndiag > 0 &&
+      (cudaMemcpy(part.data(), h->dlogdet, sizeof(double) * h->ndiag, cudaMemcpyDeviceToHost) != cudaSuccess ||
+       cudaMemcpy(bad.data(), h->dbad, sizeof(int32_t) * h->ndiag, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return STILES_ERR_CUDA;
+  for (int m = 0; m < h->count; ++m) {
+    double acc = 0.0;
+    bool spd = true;
+    for (int q = h->diag_base[m]; q < h->diag_base[m + 1]; ++q) {
+      acc += part[q];  // fixed order: tile column, then block (as for one matrix)
+      spd = spd && bad[q] < 0;
+    }
+    out_host[m] = spd ? 2.0 * acc : __builtin_nan("");
+  }
+  return STILES_OK;
+}
+
+extern "C" int stiles_batch_set_option(stiles_batch_t h, int option, long long value) {
+  if (!h) return STILES_ERR_INVALID_ARG;
+  switch (option) {
+    case STILES_OPT_WAIT_BUDGET_NS:
+      if (value <= 0) return STILES_ERR_INVALID_ARG;
+      h->budget_ns = value;
+      return STILES_OK;
+    case STILES_OPT_GRID:
+      if (value < 0 || value > 65535) return STILES_ERR_INVALID_ARG;
+      h->grid = value == 0 ? h->sms * kCtasPerSm : (int)value;
+      return STILES_OK;
+    default:
+      return STILES_ERR_INVALID_ARG;
+  }
+}
+
+extern "C" int stiles_batch_stats(stiles_batch_t h, long long stats[8]) {
+  if (!h || !stats) return STILES_ERR_INVALID_ARG;
+  stats[0] = h->dev.ntasks;
+  stats[1] = 0;
+  stats[2] = 0;
+  stats[3] = h->plan.nctr;
+  stats[4] = (long long)h->plan.flops;
+  stats[5] = h->plan.tile_gemms;
+  stats[6] = (long long)h->plan.cp_ns;
+  stats[7] = (long long)h->plan.makespan_ns;
+  return STILES_OK;
+}
+
+extern "C" int stiles_batch_destroy(stiles_batch_t h) {
+  if (!h) return STILES_ERR_INVALID_ARG;
+  if (h->launched) {
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->last_stream);
+  }
+  free_batch(h);
+  return STILES_OK;
+}
+
+extern "C" int stiles_debug_validate_batch(int count, const int* nt, const int* b, const int* band, const int* arrow,
+                                           int precision, const int* tuning) {
+  if (count < 1 || !nt || !b || !band || !arrow || precision < 0 || precision > PREC_FP32X) return STILES_ERR_INVALID_ARG;
+  std::vector<Shape> shapes;
+  std::vector<int64_t> base;
+  int64_t off = 0;
+  for (int m = 0; m < count; ++m) {
+    const int tune = tuning ? tuning[m] : 0;
+    if (nt[m] < 1 || b[m] < 1 || band[m] < 0 || arrow[m] < 0 || !tune_valid(tune)) return STILES_ERR_INVALID_ARG;
+    shapes.push_back(Shape{nt[m], b[m], band[m] < nt[m] - 1 ? band[m] : nt[m] - 1, arrow[m], precision, tune});
+    base.push_back(off);
+    off = (int64_t)align_up((size_t)(off + Layout(shapes.back()).doubles()), 32);
+  }
+  Plan p;
+  std::vector<int32_t> diag_base;
+  const int rc = build_batch_plan(shapes, base, 304, &p, &diag_base);
+  return rc ? rc : validate_plan_len(p, off, PLAN_FUSED);
 }

@@ -81,11 +81,16 @@ struct KParams {
   double* logdet_part;  // one partial sum of log diag(L) per POTRF task
   double* buf[4];       // BUF_A, BUF_L, BUF_S, BUF_W base pointers
   long long budget_ns;  // bound of one dependency wait
+  int32_t* badpiv;     // optional: per POTRF task, first failing pivot (0-based in its block) or -1
   unsigned long long* trace;  // optional: 4 words per task (claim, ready, end ns; sm/cta/op), or null
   long long buf_len;          // doubles in each of buf[0..3] (self-checking builds)
 };
 
 size_t kernel_smem_bytes();
+int kernel_threads();
+// Sets the kernel's dynamic shared-memory limit (once per process).
+cudaError_t configure_persistent();
+const void* persistent_kernel_ptr();
 cudaError_t launch_persistent(const KParams& p, int grid, cudaStream_t stream);
 
 }  // namespace stiles

@@ -908,6 +908,7 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
               if (bad >= 0) {
                 atomicCAS(&p.st->code, 0, STILES_DEV_NOT_SPD);
                 atomicMin(&p.st->spd_col, (unsigned long long)tk.gcol + (unsigned long long)bad);
+                if (p.badpiv) p.badpiv[tk.diag] = bad;
               }
             }
             break;
@@ -1061,15 +1062,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
 
 size_t kernel_smem_bytes() { return sizeof(double) * (size_t)(2 * KC * LDS + FB * LDS); }
 
-cudaError_t launch_persistent(const KParams& p, int grid, cudaStream_t stream) {
+int kernel_threads() { return NTHREADS; }
+
+const void* persistent_kernel_ptr() { return (const void*)persistent_kernel; }
+
+cudaError_t configure_persistent() {
   static bool configured = false;
-  const size_t smem = kernel_smem_bytes();
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  persistent_kernel<<<grid, NTHREADS, smem, stream>>>(p);
+  if (configured) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kernel_smem_bytes());
+  if (e == cudaSuccess) configured = true;
+  return e;
+}
+
+cudaError_t launch_persistent(const KParams& p, int grid, cudaStream_t stream) {
+  cudaError_t e = configure_persistent();
+  if (e != cudaSuccess) return e;
+  persistent_kernel<<<grid, NTHREADS, kernel_smem_bytes(), stream>>>(p);
   return cudaGetLastError();
 }
 

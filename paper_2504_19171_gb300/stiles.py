@@ -46,6 +46,9 @@ EXPORTS = [
     "stiles_factor_selinv", "stiles_logdet", "stiles_status", "stiles_set_option", "stiles_plan_stats",
     "stiles_debug_check_corrupted", "stiles_debug_break_plan", "stiles_destroy", "stiles_strerror", "stiles_trace",
     "stiles_factor_selinv_noalloc", "stiles_debug_validate", "stiles_factor_selinv_host",
+    "stiles_batch_create", "stiles_batch_offsets", "stiles_batch_workspace_bytes", "stiles_batch_factor_selinv",
+    "stiles_batch_status", "stiles_batch_logdet", "stiles_batch_set_option", "stiles_batch_stats",
+    "stiles_batch_destroy", "stiles_debug_validate_batch", "stiles_create_tuned",
 ]
 
 
@@ -80,6 +83,17 @@ def _load() -> ctypes.CDLL:
         "stiles_factor_selinv_noalloc": [vp, vp, vp, vp, vp],
         "stiles_debug_validate": [i32, i32, i32, i32, i32],
         "stiles_factor_selinv_host": [vp, vp, vp, vp, vp, vp, vp, vp],
+        "stiles_batch_create": [i32, P(i32), P(i32), P(i32), P(i32), i32, P(i32), P(vp)],
+        "stiles_create_tuned": [i32, i32, i32, i32, i32, i32, P(vp)],
+        "stiles_batch_offsets": [vp, P(sz)],
+        "stiles_batch_workspace_bytes": [vp, P(sz), P(sz)],
+        "stiles_batch_factor_selinv": [vp, vp, vp, vp, vp, vp],
+        "stiles_batch_status": [vp, i32, P(i32), P(i64)],
+        "stiles_batch_logdet": [vp, P(ctypes.c_double)],
+        "stiles_batch_set_option": [vp, i32, i64],
+        "stiles_batch_stats": [vp, P(i64)],
+        "stiles_batch_destroy": [vp],
+        "stiles_debug_validate_batch": [i32, P(i32), P(i32), P(i32), P(i32), i32, P(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -101,9 +115,12 @@ def _check(rc: int, what: str) -> None:
 
 
 # ----------------------------------------------------------- C names -----
-def stiles_create(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64) -> int:
+def stiles_create(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64, tuning: int = 0) -> int:
     h = ctypes.c_void_p()
-    _check(_lib.stiles_create(nt, b, band, arrow, precision, ctypes.byref(h)), "stiles_create")
+    if tuning:
+        _check(_lib.stiles_create_tuned(nt, b, band, arrow, precision, tuning, ctypes.byref(h)), "stiles_create_tuned")
+    else:
+        _check(_lib.stiles_create(nt, b, band, arrow, precision, ctypes.byref(h)), "stiles_create")
     return h.value
 
 
@@ -200,6 +217,72 @@ def stiles_destroy(h: Optional[int]) -> None:
     _check(_lib.stiles_destroy(h), "stiles_destroy")
 
 
+# ----------------------------------------------------------- batch ----
+def _ivec(vals):
+    arr = (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def stiles_batch_create(shapes, precision: int = STILES_FP64, tuning=None) -> int:
+    """shapes: sequence of (nt, b, band, arrow); tuning: per-matrix codes or None."""
+    n = len(shapes)
+    cols = list(zip(*shapes)) if n else [[], [], [], []]
+    h = ctypes.c_void_p()
+    tun = _ivec(tuning) if tuning is not None else None
+    _check(_lib.stiles_batch_create(n, _ivec(cols[0]), _ivec(cols[1]), _ivec(cols[2]), _ivec(cols[3]), precision,
+                                    tun, ctypes.byref(h)), "stiles_batch_create")
+    return h.value
+
+
+def stiles_batch_offsets(h: int, count: int) -> np.ndarray:
+    off = (ctypes.c_size_t * (count + 1))()
+    _check(_lib.stiles_batch_offsets(h, off), "stiles_batch_offsets")
+    return np.array(off[:], dtype=np.int64)
+
+
+def stiles_batch_workspace_bytes(h: int) -> Tuple[int, int]:
+    bb, sb = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.stiles_batch_workspace_bytes(h, ctypes.byref(bb), ctypes.byref(sb)), "stiles_batch_workspace_bytes")
+    return bb.value, sb.value
+
+
+def stiles_batch_factor_selinv(h: int, A_ptr: int, L_ptr: int, S_ptr: int, scratch_ptr: int, stream: int = 0) -> None:
+    _check(_lib.stiles_batch_factor_selinv(h, A_ptr, L_ptr, S_ptr, scratch_ptr, stream), "stiles_batch_factor_selinv")
+
+
+def stiles_batch_status(h: int, index: int) -> Tuple[int, int]:
+    code, info = ctypes.c_int(), ctypes.c_longlong()
+    _check(_lib.stiles_batch_status(h, index, ctypes.byref(code), ctypes.byref(info)), "stiles_batch_status")
+    return code.value, info.value
+
+
+def stiles_batch_logdet(h: int, count: int) -> Tuple[int, np.ndarray]:
+    out = (ctypes.c_double * count)()
+    rc = _lib.stiles_batch_logdet(h, out)
+    return rc, np.array(out[:], dtype=np.float64)
+
+
+def stiles_batch_set_option(h: int, option: int, value: int) -> None:
+    _check(_lib.stiles_batch_set_option(h, option, value), "stiles_batch_set_option")
+
+
+def stiles_batch_stats(h: int) -> Dict[str, int]:
+    st = (ctypes.c_longlong * 8)()
+    _check(_lib.stiles_batch_stats(h, st), "stiles_batch_stats")
+    keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns"]
+    return dict(zip(keys, st[:]))
+
+
+def stiles_batch_destroy(h: Optional[int]) -> None:
+    _check(_lib.stiles_batch_destroy(h), "stiles_batch_destroy")
+
+
+def stiles_debug_validate_batch(shapes, precision: int = STILES_FP64, tuning=None) -> int:
+    cols = list(zip(*shapes))
+    return _lib.stiles_debug_validate_batch(len(shapes), _ivec(cols[0]), _ivec(cols[1]), _ivec(cols[2]),
+                                            _ivec(cols[3]), precision, _ivec(tuning) if tuning is not None else None)
+
+
 # --------------------------------------------------------- layout -----
 class PackedLayout:
     """Offsets of the packed band+arrow layout (column-major tiles; see the
@@ -259,7 +342,7 @@ class Stiles:
     """One handle plus its device buffers (torch float64 tensors on CUDA)."""
 
     def __init__(self, nt: int, b: int, band: int, arrow: int, device: str = "cuda", wait_budget_s: float = None,
-                 precision: int = STILES_FP64):
+                 precision: int = STILES_FP64, tuning: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -267,7 +350,7 @@ class Stiles:
         self.torch = torch
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
-            self.h = stiles_create(nt, b, band, arrow, precision)
+            self.h = stiles_create(nt, b, band, arrow, precision, tuning)
         self.layout = PackedLayout(nt, b, band, arrow)
         self.nt, self.b, self.w, self.a = nt, b, self.layout.w, arrow
         Lb, Sb, Wb = stiles_workspace_bytes(self.h)
@@ -333,6 +416,83 @@ class Stiles:
     def close(self) -> None:
         if getattr(self, "h", None):
             stiles_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class StilesBatch:
+    """One batch handle plus its device buffers: every matrix of `shapes`
+    ((nt, b, band, arrow) each) is factored and inverted by one graph launch."""
+
+    def __init__(self, shapes, device: str = "cuda", wait_budget_s: float = None, precision: int = STILES_FP64,
+                 tuning=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("stiles needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.count = len(self.shapes)
+        with torch.cuda.device(self.device):
+            self.h = stiles_batch_create(self.shapes, precision, tuning)
+        self.off = stiles_batch_offsets(self.h, self.count)
+        self.layouts = [PackedLayout(*sh) for sh in self.shapes]
+        nbytes, sbytes = stiles_batch_workspace_bytes(self.h)
+        self.doubles = nbytes // 8
+        self.L = torch.empty(self.doubles, dtype=torch.float64, device=self.device)
+        self.S = torch.empty(self.doubles, dtype=torch.float64, device=self.device)
+        self.scratch = torch.empty(sbytes, dtype=torch.uint8, device=self.device)
+        self.A = None
+        if wait_budget_s is not None:
+            stiles_batch_set_option(self.h, STILES_OPT_WAIT_BUDGET_NS, int(wait_budget_s * 1e9))
+
+    def pack(self, mats, out: np.ndarray = None) -> np.ndarray:
+        """Host array of the batch layout holding every ArrowheadTiles of `mats`."""
+        out = np.zeros(self.doubles) if out is None else out
+        for m, M in enumerate(mats):
+            lay = self.layouts[m]
+            lay.pack(M.tiles, out[self.off[m]:self.off[m] + lay.doubles])
+        return out
+
+    def upload(self, mats) -> "StilesBatch":
+        self.A = self.torch.from_numpy(self.pack(mats)).to(self.device)
+        return self
+
+    def stream_ptr(self, stream=None) -> int:
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return int(s.cuda_stream)
+
+    def factor_selinv(self, stream=None) -> None:
+        stiles_batch_factor_selinv(self.h, self.A.data_ptr(), self.L.data_ptr(), self.S.data_ptr(),
+                                   self.scratch.data_ptr(), self.stream_ptr(stream))
+
+    def status(self, index: int) -> Tuple[int, int]:
+        return stiles_batch_status(self.h, index)
+
+    def logdet(self) -> np.ndarray:
+        rc, v = stiles_batch_logdet(self.h, self.count)
+        _check(rc, "stiles_batch_logdet")
+        return v
+
+    def _unpack(self, flat: np.ndarray, m: int):
+        lay = self.layouts[m]
+        return lay.unpack(flat[self.off[m]:self.off[m] + lay.doubles])
+
+    def sigma_tiles(self, m: int, host: np.ndarray = None):
+        return self._unpack(self.S.cpu().numpy() if host is None else host, m)
+
+    def L_tiles(self, m: int, host: np.ndarray = None):
+        return self._unpack(self.L.cpu().numpy() if host is None else host, m)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            stiles_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

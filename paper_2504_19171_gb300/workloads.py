@@ -26,6 +26,9 @@ Recipes (all use ``numpy.random.default_rng(seed)``):
 * :func:`ar1_tridiagonal`, :func:`toeplitz_tridiagonal` -- scalar (b = 1)
   tridiagonal cases with closed-form inverses.
 * :func:`batch_shapes` -- shape draws for uneven batches.
+* :func:`random_arrowhead_packed` -- the :func:`random_arrowhead` recipe
+  drawn on a torch device straight into the packed band+arrow layout (for
+  batches of many large matrices; its random stream is torch's, not numpy's).
 """
 from __future__ import annotations
 
@@ -261,3 +264,59 @@ def batch_shapes(count: int = 64, seed: int = 0, nt_range=(20, 200), b_choices=(
         a = int(rng.integers(a_range[0], a_range[1] + 1))
         out.append((nt, b, w, a))
     return out
+
+
+def random_arrowhead_packed(nt: int, b: int, w: int, a: int, seed: int, out, scale: float = 0.1) -> None:
+    """Fill the float64 torch tensor ``out`` (at least nt*colstride + a*a
+    elements, any device) with a random strictly diagonally dominant SPD
+    arrowhead matrix in the packed band+arrow layout: column-major tiles,
+    tile column k at k*colstride with colstride = (1+w) b^2 + a b, tiles
+    (k,k), (k+1,k) .. (k+w,k), (nt,k) in that slot, the corner at
+    nt*colstride. Same recipe as :func:`random_arrowhead` (off-diagonal
+    N(0,1)*scale, diagonal tiles symmetric, diagonal 1 + full-row absolute
+    sum), drawn with a torch generator seeded by ``seed``."""
+    import torch
+
+    w = min(w, nt - 1)
+    dev = out.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    colstride = (1 + w) * b * b + a * b
+    n = nt * b + a
+    rows = lambda i: a if i == nt else b  # noqa: E731
+    start = lambda i: i * b  # noqa: E731  (the arrow starts at nt*b)
+
+    def view(i, k):
+        if k == nt:
+            off = nt * colstride
+        elif i == nt:
+            off = k * colstride + (1 + w) * b * b
+        else:
+            off = k * colstride + (i - k) * b * b
+        r, c = rows(i), rows(k)
+        return out[off:off + r * c].view(c, r).t()
+
+    pattern = []
+    for k in range(nt):
+        pattern.append((k, k))
+        pattern += [(i, k) for i in range(k + 1, min(k + w, nt - 1) + 1)]
+        if a > 0:
+            pattern.append((nt, k))
+    if a > 0:
+        pattern.append((nt, nt))
+    rowabs = torch.zeros(n, dtype=torch.float64, device=dev)
+    for i, k in pattern:
+        r, c = rows(i), rows(k)
+        T = torch.randn((r, c), generator=gen, dtype=torch.float64, device=dev) * scale
+        if i == k:
+            T = torch.tril(T, -1)
+            T = T + T.t()
+            rowabs[start(i):start(i) + r] += T.abs().sum(dim=1)
+        else:
+            absT = T.abs()
+            rowabs[start(i):start(i) + r] += absT.sum(dim=1)
+            rowabs[start(k):start(k) + c] += absT.sum(dim=0)
+        view(i, k).copy_(T)
+    for i in range(nt + (1 if a > 0 else 0)):
+        r = rows(i)
+        view(i, i).diagonal().copy_(1.0 + rowabs[start(i):start(i) + r])

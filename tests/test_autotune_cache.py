@@ -1,0 +1,25 @@
+"""Autotuner bookkeeping without a GPU: the key groups shapes by
+(b, w, arrow blocks, precision) and cached choices are returned as stored."""
+import json
+
+from paper_2504_19171_gb300 import autotune as AT
+
+
+def test_key_groups_arrow_by_blocks():
+    assert AT.key_of(256, 2, 1, 0) == AT.key_of(256, 2, 64, 0)
+    assert AT.key_of(256, 2, 65, 0) != AT.key_of(256, 2, 64, 0)
+    assert AT.key_of(256, 2, 64, 1) != AT.key_of(256, 2, 64, 0)
+
+
+def test_cached_choice_is_used(tmp_path):
+    p = tmp_path / "t.json"
+    p.write_text(json.dumps({AT.key_of(512, 3, 100, 1): {"code": 24, "seconds": {"0": 1.0, "24": 0.5}}}))
+    t = AT.Autotuner(str(p))
+    assert t.best(512, 3, 100, 1) == 24
+    assert t.codes_for([(50, 512, 3, 128)], 1) == [24]
+
+
+def test_candidates_are_valid_tuning_codes():
+    from paper_2504_19171_gb300 import stiles as S
+    for c in AT.CANDIDATES:
+        assert S.stiles_debug_validate(5, 64, 1, 8, S.PLAN_FUSED + 256 * c) == S.STILES_OK
