@@ -83,12 +83,14 @@ enum stiles_status_code {
  * always run in FP64.
  *   STILES_FP64   IEEE binary64 on the FP64 pipe.
  *   STILES_EMU64  emulated FP64: every operand is split, per row / column of
- *                 its panel, into six signed 8-bit integer digits held
- *                 exactly in bf16; digit products run on the tensor cores
- *                 with exact FP32 accumulation per K chunk, move into int32
- *                 level sums and are recombined in FP64 (split-precision
- *                 scheme of Ozaki, Ogita, Oishi and Rump). Relative error of a
- *                 product about 2^-47 of (max |row| x max |column|).
+ *                 its panel, into seven 8-bit integer digits (56-bit fixed
+ *                 point, the entry's sign on each) held exactly in bf16;
+ *                 digit products run on the tensor cores with exact FP32
+ *                 accumulation per K chunk, move into int32 level sums and
+ *                 are recombined exactly in 128-bit integers, then rounded to
+ *                 FP64 (split-precision scheme of Ozaki, Ogita, Oishi and
+ *                 Rump). Error of a product term about 8 x 2^-56 of
+ *                 (max |row| x max |column|).
  *   STILES_FP32X  FP32-class: operands rounded to FP32, FP32 FMA accumulation. */
 enum stiles_precision { STILES_FP64 = 0, STILES_EMU64 = 1, STILES_FP32X = 2 };
 

@@ -420,16 +420,25 @@ __device__ __forceinline__ void accumulate_f32(const KParams& p, const Task& tk,
 //
 // Error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump: for one
 // segment, every row i of op(A) gets the exponent E_i of its largest entry
-// and every column j of op(B) the exponent F_j; each entry becomes a 48-bit
-// fixed-point integer relative to that exponent, cut into EMU_S = 6 signed
-// 8-bit digits, which bf16 holds exactly. A product of two digits is an exact
-// 16-bit integer; a sum of at most 6 x 32 of them stays below 2^24, so the
-// FP32 tensor-core accumulation of one K chunk is exact and is moved into an
-// int32 accumulator per level L = t + u (digit weights 2^-8t, 2^-8u). Levels
-// L <= EMU_S - 1 are kept (the rest weigh less than 2^-48 relative), and the
-// levels are recombined in FP64 with the scale 2^(E_i + F_j) at the end.
-constexpr int EMU_S = 6;
-constexpr int EMU_KP = 40;  // padded digit-row length (bf16) in shared memory
+// and every column j of op(B) the exponent F_j; each entry becomes a 56-bit
+// fixed-point integer relative to that exponent (the largest entry keeps all
+// 53 bits of its significand), cut into EMU_S = 7 unsigned 8-bit digits
+// carrying the entry's sign, which bf16 holds exactly. A product of two digits
+// is an exact 16-bit integer; a sum of at most 7 x 32 of them stays below
+// 2^24, so the FP32 tensor-core accumulation of one K chunk is exact and is
+// moved into an int32 accumulator per level L = t + u (digit weights 2^-8t,
+// 2^-8u). Levels L <= EMU_S - 1 are kept (the dropped ones and the operand
+// truncation weigh about (EMU_S + 1) 2^-56 of max|row| max|column| per
+// product), and the levels are recombined exactly in 128-bit integers, then
+// scaled by 2^(E_i + F_j).
+constexpr int EMU_S = 7;
+constexpr int EMU_KP = 36;  // padded digit-row length (bf16) in shared memory
+// An operand of biased exponent e <= emax has the fixed-point value m 2^(e - emax + 8 EMU_S - 53);
+// the product of two then carries the scale 2^(E_i + F_j - kEmuScale).
+constexpr int kEmuScale = 2 * (1075 + 8 * EMU_S - 53);
+static_assert(2 * EMU_S * 32 * EMU_KP * 2 <= 2 * KC * LDS * 8, "digit panels must fit the staging region");
+static_assert(EMU_S * 8 * NTHREADS * 4 + 64 * 4 <= FB * LDS * 8, "level sums must fit the block region");
+static_assert(EMU_S * 32 * 255 * 255 < (1 << 24), "one K chunk of a level must be exact in FP32");
 
 __device__ __forceinline__ int biased_exp(double v) {
   return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
@@ -441,8 +450,8 @@ __device__ __forceinline__ void emu_digits(double v, int emax, uint16_t (&d)[EMU
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((bits >> 52) & 0x7ff);
   const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-  const int shift = 5 + emax - (e ? e : 1);
-  const unsigned long long X = shift >= 64 ? 0ull : (m >> shift);  // < 2^48
+  const int shift = emax - (e ? e : 1) - (8 * EMU_S - 53);  // >= -(8 EMU_S - 53)
+  const unsigned long long X = shift >= 64 ? 0ull : shift >= 0 ? (m >> shift) : (m << -shift);  // < 2^(8 EMU_S)
   const uint16_t sgn = (uint16_t)((bits >> 48) & 0x8000u);
 #pragma unroll
   for (int t = 0; t < EMU_S; ++t) {
@@ -513,7 +522,8 @@ __device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, 
     emu_max_exp(A, gs.lda, !ta, sb.rm, gs.k, rexp);
     emu_max_exp(B, gs.ldb, tb, sb.cn, gs.k, cexp);
     __syncthreads();
-    // int32 level sums stay exact for 6 * 4096 * 255^2 < 2^31: recombine every 4096 of K
+    static_assert((long long)EMU_S * 4096 * 255 * 255 < (1ll << 31), "level sums over 4096 of K must fit int32");
+    // int32 level sums stay exact for EMU_S * 4096 * 255^2 < 2^31: recombine every 4096 of K
     for (int kb = 0; kb < gs.k; kb += 4096) {
       const int kend = min(gs.k, kb + 4096);
 #pragma unroll
@@ -592,7 +602,7 @@ __device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, 
         __syncthreads();
       }
       // recombine exactly in 128-bit integers: V = sum_L lev_L 2^(8 (EMU_S - 1 - L)),
-      // then one rounding to FP64 and the scale 2^(E_i + F_j - 2140 + 8 (EMU_S - 1))
+      // then one rounding to FP64 and the scale 2^(E_i + F_j - kEmuScale + 8 (EMU_S - 1))
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -605,7 +615,7 @@ __device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, 
           const unsigned long long vl = (unsigned long long)V;
           const double v = fma((double)vh, 18446744073709551616.0, (double)vl);
           const int row = 16 * wr + g + 8 * (q >> 1), col = 16 * wc + 8 * j + 2 * tq + (q & 1);
-          const int k2 = rexp[row] + cexp[col] - 2140 + 8 * (EMU_S - 1);
+          const int k2 = rexp[row] + cexp[col] - kEmuScale + 8 * (EMU_S - 1);
           // 2^k2 built from its exponent bits when it is a normal double
           const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
           res[j][q] = fma(v, sc, res[j][q]);
