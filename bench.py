@@ -361,6 +361,129 @@ def run_batched(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+SERVE = {"workload": "served_sweep_requests", "pool": "64 shapes of the batched draw (seed 0)",
+         "arrivals": "Poisson, 200 requests/s (seed 1)", "tau": "U[0.1, 10]", "rho": "U[0.5, 0.99]",
+         "values": "per shape: base off-diagonal N(0,1)*0.1 (torch generator, seed 2000 + shape); per request: "
+                   "band x rho, arrow as is, diagonal tau + rho rb + ra"}
+
+
+def run_serving(args, world, rank, local):
+    """Request server: open-loop Poisson arrivals over a fixed window (queueing
+    delay included in the latency), then a closed loop at fixed concurrency."""
+    import numpy as np
+    import torch
+
+    from paper_2504_19171_gb300 import build as B
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    from paper_2504_19171_gb300 import autotune as AT
+    from paper_2504_19171_gb300 import stiles as S
+    from paper_2504_19171_gb300 import workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    pool = W.batch_shapes(64, seed=0)
+    prec = {"fp64": S.STILES_FP64, "emu64": S.STILES_EMU64, "fp32x": S.STILES_FP32X}[args.precision]
+    tuner = AT.Autotuner(AT.default_cache_path())
+    flops = [S.stiles_plan_stats(*sh, S.PLAN_FUSED, 152)["flops"] for sh in pool]
+    t0 = time.perf_counter()
+    srv = S.StilesServer(pool, int(args.serve_gb * 2**30), max_requests=256, precision=prec,
+                         tuning=tuner.codes_for(pool, prec), device=str(dev))
+    for m, sh in enumerate(pool):
+        d, n = srv.shape_doubles(m)
+        base = torch.zeros(d, dtype=torch.float64, device=dev)
+        rb, ra = W.sweep_base_packed(*sh, 2000 + m, base)
+        srv.set_base(m, base, rb, ra)
+        del base
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(1)
+
+    def draw(count):
+        return [(int(rng.integers(0, len(pool))), float(rng.uniform(0.1, 10.0)), float(rng.uniform(0.5, 0.99)))
+                for _ in range(count)]
+
+    def run_phase(arrivals, reqs, window, closed_conc=0):
+        """arrivals: times (s) or None for the closed loop; returns stats."""
+        srv.start(window + 120.0)
+        queue, start_t, lat, done_flops, done_n, failed = [], {}, [], 0.0, 0, 0
+        tag = 0
+        t_start = time.perf_counter()
+        in_flight = 0
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t_start
+            if arrivals is not None:
+                while nxt < len(arrivals) and arrivals[nxt] <= now and arrivals[nxt] < window:
+                    queue.append((nxt, arrivals[nxt]))
+                    nxt += 1
+            else:
+                while now < window and in_flight + len(queue) < closed_conc:
+                    queue.append((nxt, now))
+                    nxt += 1
+            while queue:
+                i, t_arr = queue[0]
+                shape, tau, rho = reqs[i % len(reqs)]
+                r = srv.submit(shape, tau, rho, tag=i)
+                if r is None:
+                    break
+                queue.pop(0)
+                start_t[i] = (t_arr, shape)
+                in_flight += 1
+            for r, i in srv.poll():
+                t_arr, shape = start_t.pop(i)
+                code = srv.result(r)[0]
+                srv.release(r)
+                in_flight -= 1
+                if code != S.STILES_OK:
+                    failed += 1
+                    continue
+                done_n += 1
+                done_flops += flops[shape]
+                lat.append(time.perf_counter() - t_start - t_arr)
+            if now >= window and (arrivals is None or True):
+                if in_flight == 0 or now > window + 100.0:
+                    break
+                queue.clear()  # arrivals after the window are not offered
+            time.sleep(0.0005)
+        elapsed = time.perf_counter() - t_start
+        status = srv.stop()
+        lat_ms = np.array(lat) * 1e3
+        return {"completed": done_n, "failed": failed, "left_unadmitted_at_window_end": len(queue),
+                "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+                "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+                "served_tflops": done_flops / elapsed / 1e12, "requests_per_s": done_n / elapsed,
+                "elapsed_s": elapsed, "kernel_status": S.strerror(status)}
+
+    reqs = draw(200000)
+    arr = np.cumsum(rng.exponential(1.0 / 200.0, size=int(200 * args.serve_window * 1.2) + 10))
+    offered = sum(flops[reqs[i][0]] for i in range(len(arr)) if arr[i] < args.serve_window) / args.serve_window
+    open_loop = run_phase(list(arr), reqs, args.serve_window)
+    open_loop["offered_tflops"] = offered / 1e12
+    open_loop["offered_requests_per_s"] = float(np.sum(arr < args.serve_window)) / args.serve_window
+    closed = run_phase(None, reqs, args.serve_window, closed_conc=args.serve_concurrency)
+    closed["concurrency"] = args.serve_concurrency
+    srv.close()
+    line = {
+        "metric": "served selected-inversion requests: p50/p99 latency and throughput",
+        "value": closed["requests_per_s"], "unit": "requests/s (closed loop)", "n_gpus": world,
+        "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": dict(SERVE, window_s=args.serve_window, data_arena_gb=args.serve_gb,
+                       parallelism=f"replicas{world}" if world > 1 else "single"),
+        "open_loop": open_loop, "closed_loop": closed, "setup_s": setup_s,
+        "e2e": None, "gpu_launches": 2,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -490,8 +613,13 @@ def main():
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],
                     help="tile columns (default 200; smaller values are profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="spatiotemporal", choices=["spatiotemporal", "batched"],
-                    help="spatiotemporal: the n = 204,864 matrix (default); batched: 64 uneven matrices per launch")
+    ap.add_argument("--workload", default="spatiotemporal", choices=["spatiotemporal", "batched", "serving"],
+                    help="spatiotemporal: the n = 204,864 matrix (default); batched: 64 uneven matrices per "
+                         "launch; serving: request server under Poisson arrivals")
+    ap.add_argument("--precision", default="emu64", choices=["fp64", "emu64", "fp32x"], help="serving precision")
+    ap.add_argument("--serve-window", type=float, default=30.0, help="serving: seconds of arrivals per phase")
+    ap.add_argument("--serve-gb", type=float, default=120.0, help="serving: data arena (GiB)")
+    ap.add_argument("--serve-concurrency", type=int, default=16, help="serving: requests in flight (closed loop)")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default tuning codes")
     args = ap.parse_args()
     world, rank, local = dist_init()
@@ -499,6 +627,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

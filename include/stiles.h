@@ -74,7 +74,8 @@ enum stiles_status_code {
   STILES_ERR_OOM = -5,         /* host or device allocation for the handle failed */
   STILES_ERR_UNSUPPORTED = -6, /* precision or option not available */
   STILES_ERR_PLAN = -7,        /* a task table failed its consistency check */
-  STILES_ERR_TOO_LARGE = -8    /* the shape's scratch does not fit the fixed no-allocation array */
+  STILES_ERR_TOO_LARGE = -8,   /* the shape's scratch does not fit the fixed no-allocation array */
+  STILES_ERR_BUSY = -9         /* request server: no memory or slot free now (retry after a release) */
 };
 
 /* Precision of the off-diagonal bulk products (the factor's GEMM/SYRK
@@ -327,12 +328,93 @@ int stiles_batch_set_option(stiles_batch_t h, int option, long long value);
 /* Plan statistics of the merged table (same fields as stiles_plan_stats). */
 int stiles_batch_stats(stiles_batch_t h, long long stats[8]);
 
+/* --------------------------------------------------------------- server --
+ * Request server with continuous batching (no counterpart in the paper; its
+ * use case is the hyperparameter sweep of INLA-type models, where many
+ * selected inversions of matrices with a fixed pattern and varying values are
+ * needed). One persistent kernel keeps running; requests are admitted while
+ * others execute and their tasks share the GPU with them.
+ *
+ * A request names a pool shape and two value parameters: its matrix is the
+ * shape's base matrix B (set once) rescaled as
+ *     A = rho * (band entries of B) + (arrow entries of B),
+ *     diag(A)_i = tau + rho * rb_i + ra_i,
+ * with rb / ra the caller's band / arrow absolute row sums of B (so A stays
+ * strictly diagonally dominant for every tau > 0, rho > 0 when B's diagonal
+ * is). The kernel builds A in the request's own memory (one task per tile
+ * column), factors it in place and computes Sigma on L's pattern.
+ *
+ * Memory. stiles_server_create allocates everything once: base values of
+ * every shape, a data arena of data_bytes from which each request takes its
+ * L, Sigma and scratch (3 x stiles_layout_doubles of its shape, rounded up to
+ * 32 doubles; stiles_server_request_bytes), task-table arenas for
+ * max(4, max_requests) copies of the largest shape, ready rings and a pinned,
+ * host-mapped control block. stiles_server_submit returns STILES_ERR_BUSY if
+ * the request does not fit now (admission by HBM footprint): retry after a
+ * stiles_server_release.
+ *
+ * Threading: the functions of one server are called from one host thread. */
+typedef struct stiles_server *stiles_server_t;
+
+/* Pool of nshapes shapes (as for stiles_create), one precision, optional
+ * per-shape tuning codes, data arena bytes, request slots (1 .. 1024). */
+int stiles_server_create(int nshapes, const int *nt, const int *b, const int *band, const int *arrow, int precision,
+                         const int *tuning, size_t data_bytes, int max_requests, stiles_server_t *out);
+
+/* Packed-layout doubles and matrix order n of a pool shape. */
+int stiles_server_shape_doubles(stiles_server_t h, int shape, size_t *doubles, size_t *n);
+
+/* Base matrix of a shape (packed layout, stiles_server_shape_doubles
+ * doubles) and its band / arrow absolute row sums (n doubles each); host or
+ * device pointers. Every shape needs one before stiles_server_start. */
+int stiles_server_set_base(stiles_server_t h, int shape, const double *base, const double *rb, const double *ra);
+
+/* Launch the server kernel (on the server's own stream). Idle workers give up
+ * window_s seconds after the launch (STILES_ERR_TIMEOUT from
+ * stiles_server_stop): a bound, so that a host that never stops the server
+ * cannot keep the GPU. */
+int stiles_server_start(stiles_server_t h, double window_s);
+
+/* Admit a request of pool shape `shape` with (tau, rho); `tag` is returned by
+ * stiles_server_poll. On STILES_OK *request is its slot. STILES_ERR_BUSY if
+ * no memory or slot is free now. */
+int stiles_server_submit(stiles_server_t h, int shape, double tau, double rho, long long tag, int *request);
+
+/* Requests completed since the last poll, each reported once (up to max). */
+int stiles_server_poll(stiles_server_t h, int max, int *requests, long long *tags, int *n_out);
+
+/* Status (STILES_OK / STILES_ERR_NOT_SPD with the 1-based failing column in
+ * *info) and logdet (NaN unless OK) of a completed request. */
+int stiles_server_result(stiles_server_t h, int request, int *code, long long *info, double *logdet);
+
+/* Sigma of a completed request (packed layout of its shape): copied to
+ * host_out (host or device memory) if not NULL, and/or its device address in
+ * *device_ptr (valid until the request is released). */
+int stiles_server_sigma(stiles_server_t h, int request, double *host_out, const double **device_ptr);
+
+/* Free a completed request's memory, tables and slot. */
+int stiles_server_release(stiles_server_t h, int request);
+
+/* Data-arena bytes a request of `shape` takes. */
+int stiles_server_request_bytes(stiles_server_t h, int shape, size_t *bytes);
+
+/* Ask the kernel to stop once idle (call after every request completed) and
+ * wait for it. STILES_OK, or STILES_ERR_TIMEOUT if the window ran out. */
+int stiles_server_stop(stiles_server_t h);
+
+/* Stops the kernel if running, frees everything. */
+int stiles_server_destroy(stiles_server_t h);
+
 /* Test hook (host only, no device): build the merged table of a batch and
  * emulate a launch of it (bounds of every access within the batch buffers,
  * queue capacities, every task released once). Returns STILES_OK or
  * STILES_ERR_PLAN. */
 int stiles_debug_validate_batch(int count, const int *nt, const int *b, const int *band, const int *arrow,
                                 int precision, const int *tuning);
+
+/* Test hook (host only): build the request-server table of one shape and
+ * emulate a launch of it (as stiles_debug_validate). */
+int stiles_debug_validate_serve(int nt, int b, int band, int arrow, int precision, int tuning);
 
 /* Waits for the last launch, frees the tables, the graph and the handle. */
 int stiles_batch_destroy(stiles_batch_t h);

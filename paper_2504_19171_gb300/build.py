@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libstiles.so")
-SOURCES = ["stiles_kernel.cu", "stiles_api.cu", "plan.cpp"]
+SOURCES = ["stiles_kernel.cu", "stiles_api.cu", "stiles_server.cu", "plan.cpp"]
 HEADERS = ["plan.h", "stiles_device.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -59,6 +59,9 @@ struct Builder {
   long long tile_gemms = 0;
   int ndiag = 0;
 
+  bool serve = false;                // emit OP_PREP tasks (request server template)
+  std::vector<int32_t> prep_ctr;     // serve: per tile column, signalled by its PREP task
+
   Builder(const Shape& sh, PlanKind k, Plan* o) : s(sh), L(sh), kind(k), out(o) {}
 
   int32_t newctr(bool is_chain) {
@@ -193,6 +196,7 @@ struct Builder {
             if (kind == PLAN_FUSED) colblocks[k]++;
           }
     }
+    if (serve) emit_prep(cols);
     // emit per fine column q = (kq, cq) in order: the chains into each block
     // of that column, then its final POTRF / TRSM.
     for (int kq = 0; kq < cols; ++kq) {
@@ -204,6 +208,31 @@ struct Builder {
         for (int i : tiles_below)
           for (int r = (i == kq ? cq : 0); r < L.nblk(i); ++r) emit_block_chain(i, r, kq, cq);
       }
+    }
+  }
+
+  // Request server: one PREP task per tile column (the only roots).
+  void emit_prep(int cols) {
+    prep_ctr.resize(cols);
+    const int64_t n = (int64_t)s.nt * s.b + s.a;
+    for (int k = 0; k < cols; ++k) {
+      prep_ctr[k] = newctr(false);
+      Task t = blank(OP_PREP, 0, 0);
+      const int64_t slot = L.tile(k, k);
+      t.out = mkref(BUF_L, slot);
+      t.cin = mkref(BUF_A, slot);
+      const int64_t row0 = (int64_t)k * s.b;
+      t.aux = mkref(BUF_A, L.doubles() + row0);
+      t.ldo = s.b;
+      t.ldc = s.a;
+      t.ldx = L.nsub(k);
+      t.zrows = s.w;
+      t.diag = (int32_t)row0;
+      t.gcol = (int32_t)n;
+      if (k == s.nt) t.flags |= TF_CORNER;
+      t.flags |= TF_URGENT * (k == 0);
+      const double elems = k == s.nt ? (double)s.a * s.a : (double)(1 + L.nsub(k)) * s.b * s.b + (double)s.a * s.b;
+      emit(t, {}, {}, {prep_ctr[k]}, elems * 0.02);
     }
   }
 
@@ -283,6 +312,7 @@ struct Builder {
       lower_precision(tk);
       std::vector<Wait> w;
       if (nwritten > 0) w.push_back({me, nwritten});
+      if (nwritten == 0 && serve) w.push_back({prep_ctr[kq], 1});
       term_waits(terms[t], w);
       emit(tk, {term_seg(terms[t])}, w, {me}, 0.0);
       ++nwritten;
@@ -291,6 +321,7 @@ struct Builder {
     std::vector<Seg> segs;
     std::vector<Wait> w;
     if (nwritten > 0) w.push_back({me, nwritten});
+    if (nwritten == 0 && serve) w.push_back({prep_ctr[kq], 1});
     for (size_t t = nchain; t < terms.size(); ++t) {
       segs.push_back(term_seg(terms[t]));
       term_waits(terms[t], w);
@@ -703,6 +734,19 @@ int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out) {
   return check_plan(*out);
 }
 
+int build_serve_template(const Shape& s, int workers, Plan* out) {
+  if (!shape_ok(s)) return STILES_ERR_INVALID_ARG;
+  if (task_estimate(s) > 4.0e8) return STILES_ERR_INVALID_ARG;
+  Builder B(s, PLAN_FUSED, out);
+  B.serve = true;
+  B.build_factor();
+  B.build_selinv();
+  B.flops = tile_flops(s, PLAN_FUSED);
+  int rc = B.finish(workers);
+  if (rc) return rc;
+  return check_plan(*out);
+}
+
 int build_batch_plan(const std::vector<Shape>& shapes, const std::vector<int64_t>& base, int workers, Plan* out,
                      std::vector<int32_t>* diag_base) {
   if (shapes.empty() || base.size() != shapes.size() || !out || !diag_base) return STILES_ERR_INVALID_ARG;
@@ -762,7 +806,7 @@ int check_plan(const Plan& p) {
     if (tk.wait0 < 0 || tk.nwait < 0 || (int64_t)tk.wait0 + tk.nwait > (int64_t)p.waits.size()) return STILES_ERR_PLAN;
     if (tk.seg0 < 0 || tk.nseg < 0 || (int64_t)tk.seg0 + tk.nseg > (int64_t)p.segs.size()) return STILES_ERR_PLAN;
     if (tk.sig0 < 0 || tk.nsig < 0 || (int64_t)tk.sig0 + tk.nsig > (int64_t)p.sigs.size()) return STILES_ERR_PLAN;
-    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_SYMUPD) return STILES_ERR_PLAN;
+    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_PREP) return STILES_ERR_PLAN;
     if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_TILE32 || tk.prec > PREC_FP32X) return STILES_ERR_PLAN;
     for (int q = 0; q < tk.nwait; ++q) {
       const Wait& w = p.waits[tk.wait0 + q];
@@ -805,6 +849,20 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
   };
   for (int t = 0; t < nt; ++t) {
     const Task& tk = p.tasks[t];
+    if (tk.op == OP_PREP) {  // a whole tile column of the base and of L, and the row-sum vectors
+      const int64_t b = tk.ldo, a = tk.ldc, rows = (tk.flags & TF_CORNER) ? a : b;
+      const int64_t len = (tk.flags & TF_CORNER) ? a * a : (1 + (int64_t)tk.zrows) * b * b + a * b;
+      const int64_t base_lim = lim + 2 * (int64_t)tk.gcol;  // base values, then rb, ra
+      auto in_base = [&](int64_t ref, int64_t lo_off, int64_t hi_off) {
+        return ref >= 0 && (ref >> BUF_SHIFT) == BUF_A && (ref & OFF_MASK) + lo_off >= 0 &&
+               (ref & OFF_MASK) + hi_off < base_lim;
+      };
+      if (tk.parts != 1 || !in(tk.out, 0, len - 1) || !in_base(tk.cin, 0, len - 1) ||
+          !in_base(tk.aux, 0, rows - 1) || !in_base(tk.aux, tk.gcol, tk.gcol + rows - 1) ||
+          (int64_t)tk.diag + rows > (int64_t)tk.gcol)
+        return bad("PREP out of bounds", t);
+      continue;
+    }
     for (int q = 0; q < tk.parts; ++q) {
       int r0 = 0, c0 = 0, rm = tk.m, cn = tk.n;
       switch (tk.pmode) {

@@ -36,6 +36,9 @@ enum Op : uint8_t {
   OP_STORE = 5,     // out = acc
   OP_NEG = 6,       // out = -acc
   OP_SYMUPD = 7,    // out = cin - acc and its transpose into the mirror block (aux)
+  OP_PREP = 8,      // served requests: one tile column of A from the shape's base values and the
+                    // request's (rho, tau): band entries x rho, arrow entries as they are,
+                    // diagonal tau + rho rb[i] + ra[i] (rb / ra = band / arrow absolute row sums)
 };
 
 // How a task's output block is divided among CTAs (each part runs as its own
@@ -52,7 +55,7 @@ enum PartMode : uint8_t {
 // Arithmetic of a task's block products (its epilogue is always FP64).
 enum Precision : uint8_t {
   PREC_FP64 = 0,   // FP64 FMA pipe
-  PREC_EMU64 = 1,  // split-precision emulated FP64: 6 bf16 digit planes per operand on the tensor cores
+  PREC_EMU64 = 1,  // split-precision emulated FP64: 7 bf16 digit planes per operand on the tensor cores
   PREC_FP32X = 2,  // FP32 FMA pipe (FP32-class)
 };
 
@@ -60,6 +63,7 @@ enum Precision : uint8_t {
 enum TaskFlag : uint8_t {
   TF_SYM_DIAG = 1,  // OP_SYMUPD on a diagonal block (mirror inside the block)
   TF_URGENT = 2,    // on the critical path: queued ahead of the buckets
+  TF_CORNER = 4,    // OP_PREP of the arrow corner column
 };
 
 struct Seg {       // acc += op(A) (m x k) * op(B) (k x n)
@@ -199,6 +203,16 @@ int validate_plan(const Plan& p, const Shape& s, int kind);
 // The same with an explicit buffer length (doubles in each of A, L, Sigma and
 // the scratch's packed part), for batch plans.
 int validate_plan_len(const Plan& p, int64_t buf_doubles, int kind);
+
+// Fused task table of one shape for the request server: as the fused plan,
+// plus one OP_PREP task per tile column that writes the request's A (in the
+// L buffer) from the shape's base values; every task that reads a block of A
+// waits for the PREP of its tile column, and the PREP tasks are the only
+// roots. PREP fields: out = tile column slot (BUF_L), cin = the same slot of
+// the base values (BUF_A), aux = rb of the column's first row (BUF_A; ra
+// follows rb at distance gcol = n), ldo = b, ldc = a, ldx = present
+// sub-diagonal tiles, zrows = w, diag = first row of the column.
+int build_serve_template(const Shape& s, int workers, Plan* out);
 
 // One fused (factor + selected inversion) task table for a batch of
 // independent matrices: matrix m's tiles live at offset base[m] (doubles) of

@@ -843,3 +843,20 @@ extern "C" int stiles_debug_validate_batch(int count, const int* nt, const int* 
   const int rc = build_batch_plan(shapes, base, 304, &p, &diag_base);
   return rc ? rc : validate_plan_len(p, off, PLAN_FUSED);
 }
+
+extern "C" int stiles_debug_validate_serve(int nt, int b, int band, int arrow, int precision, int tuning) {
+  if (nt < 1 || b < 1 || band < 0 || arrow < 0 || precision < 0 || precision > PREC_FP32X || !tune_valid(tuning))
+    return STILES_ERR_INVALID_ARG;
+  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision, tuning};
+  Plan p;
+  const int rc = build_serve_template(sh, 304, &p);
+  if (rc) return rc;
+  int roots_prep = 0, roots = 0;
+  for (size_t t = 0; t < p.tasks.size(); ++t)
+    if (p.indeg[t] == 0) {
+      ++roots;
+      roots_prep += p.tasks[t].op == OP_PREP;
+    }
+  if (roots == 0 || roots != roots_prep) return STILES_ERR_PLAN;  // the PREP tasks are the only roots
+  return validate_plan_len(p, Layout(sh).doubles(), PLAN_FUSED);
+}

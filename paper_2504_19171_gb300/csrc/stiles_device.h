@@ -67,6 +67,44 @@ inline SchedState sched_state_at(int* base, int ntasks, int nbuckets, int ucap) 
   return s;
 }
 
+// ---- request server (continuous batching in one running kernel) ----------
+constexpr int kServeInbox = 4096;  // records in the host inbox ring (>= request slots)
+constexpr int kServeMaxReq = 1024; // request slots
+
+struct ServeRec {  // one activation, written by the host
+  int slot;        // request slot
+  int root0;       // its root tasks: roots[root0 .. root0 + nroots)
+  int nroots;
+  unsigned seq;    // sequence number, echoed in done_seq[slot] when the request completes
+  double rho, tau; // value parameters of the request (OP_PREP)
+};
+
+struct ServeCtl {  // host-mapped (pinned) control block
+  int inbox_count; // records published by the host
+  int stop;        // 1: workers exit once idle
+  int pad[30];
+  ServeRec inbox[kServeInbox];
+  unsigned done_seq[kServeMaxReq];  // written by the device (system-scope release)
+};
+
+struct ServeRing {  // ready parts of one priority class
+  int* slots;       // capacity mask + 1 entries, -1 when free
+  int* ctr;         // ctr[0] tail (reserved), ctr[8] head (claimed), ctr[16] available
+  unsigned mask;
+};
+
+struct ServeDev {
+  ServeRing ring[3];           // urgent, other factor tasks, the rest
+  ServeCtl* ctl;               // device address of the host-mapped control block
+  int* inbox_seen;             // records activated so far
+  int32_t* treq;               // task -> request slot
+  int32_t* req_left;           // per slot: tasks not yet finished
+  unsigned* req_seq;           // per slot: sequence number of the request it holds
+  double* req_param;           // per slot: rho, tau
+  int32_t* roots;              // root task lists (global task indices)
+  unsigned long long deadline; // %globaltimer value after which idle workers stop
+};
+
 struct KParams {
   const Task* tasks;
   const Seg* segs;
@@ -84,6 +122,8 @@ struct KParams {
   int32_t* badpiv;     // optional: per POTRF task, first failing pivot (0-based in its block) or -1
   unsigned long long* trace;  // optional: 4 words per task (claim, ready, end ns; sm/cta/op), or null
   long long buf_len;          // doubles in each of buf[0..3] (self-checking builds)
+  int serve;                  // 1: request server (rings and inbox instead of the static buckets)
+  ServeDev sv;
 };
 
 size_t kernel_smem_bytes();

@@ -33,6 +33,17 @@ __device__ __forceinline__ double* resolve(const KParams& p, int64_t ref) {
   return p.buf[ref >> BUF_SHIFT] + (ref & OFF_MASK);
 }
 
+// Task-table reads. A request server rewrites table ranges (copy engine)
+// while the kernel runs; a worker reads a task only after the acquire load of
+// the queue slot that delivered it, which is ordered after the host's
+// publication (system-scope release / acquire on the inbox, then release /
+// acquire through the queues), so plain loads see the new rows. (Loading
+// whole rows with L2-only vector loads instead costs registers the block
+// products need.)
+__device__ __forceinline__ Task load_task(const KParams& p, int t) { return p.tasks[t]; }
+
+__device__ __forceinline__ Seg load_seg(const KParams& p, int g) { return p.segs[g]; }
+
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -49,6 +60,15 @@ __device__ __forceinline__ int load_acquire_i(const int* a) {
 
 __device__ __forceinline__ void store_release_i(int* a, int v) {
   cuda::atomic_ref<int, cuda::thread_scope_device>(*a).store(v, cuda::memory_order_release);
+}
+
+// Host-mapped memory (request server control block).
+__device__ __forceinline__ int load_acquire_sys(const int* a) {
+  return cuda::atomic_ref<int, cuda::thread_scope_system>(*const_cast<int*>(a)).load(cuda::memory_order_acquire);
+}
+
+__device__ __forceinline__ void store_release_sys(unsigned* a, unsigned v) {
+  cuda::atomic_ref<unsigned, cuda::thread_scope_system>(*a).store(v, cuda::memory_order_release);
 }
 
 // Record a TIMEOUT (first error wins) and stop every worker.
@@ -77,9 +97,16 @@ __device__ void check_fail(const KParams& p, int what, long long t, int q) {
 // Push a ready task into the bucket of its queue position: one slot per part
 // (value 4 t + part), so that the parts run on different CTAs. The slots are
 // reserved (tail), stored, and only then counted as available.
+__device__ void serve_push(const KParams& p, int t);
+
 __device__ __forceinline__ void push_task(const KParams& p, int t) {
-  const int parts = p.tasks[t].parts;
-  if (p.tasks[t].flags & TF_URGENT) {
+  if (p.serve) {
+    serve_push(p, t);
+    return;
+  }
+  const Task tk = load_task(p, t);
+  const int parts = tk.parts;
+  if (tk.flags & TF_URGENT) {
     const int pos = atomicAdd(p.q.lo + 8, parts);
     STILES_CHECK(pos + parts <= p.ucap, 1, t, 0);
     for (int q = 0; q < parts; ++q) store_release_i(p.q.uslots + pos + q, 4 * t + q);
@@ -126,6 +153,97 @@ __device__ __forceinline__ int claim(int* avail, int* head) {
   return atomicAdd(head, 1);
 }
 
+// ---- request server: three FIFO rings (urgent, other factor tasks, rest) ---
+// Ring entries are reserved (tail), stored, then counted available, like the
+// buckets; a popped entry is reset to -1 so the ring can wrap (its capacity
+// exceeds the parts that can be ready at once).
+__device__ void serve_push(const KParams& p, int t) {
+  const Task tk = load_task(p, t);
+  const int parts = tk.parts;
+  const bool factor = tk.op == OP_UPD || tk.op == OP_POTRF || tk.op == OP_TRSM_RLT || tk.op == OP_PREP;
+  const ServeRing& R = p.sv.ring[(tk.flags & TF_URGENT) ? 0 : factor ? 1 : 2];
+  const unsigned pos = (unsigned)atomicAdd(R.ctr, parts);
+  for (int q = 0; q < parts; ++q) {
+    int* slot = R.slots + ((pos + q) & R.mask);
+    const unsigned long long start = gtimer();
+    while (load_acquire_i(slot) != -1) {  // the previous lap's entry not yet taken: bounded wait
+      if (load_relaxed_flag(&p.st->abort)) return;
+      if (gtimer() - start > (unsigned long long)p.budget_ns) {
+        raise_timeout(p, t);
+        return;
+      }
+      __nanosleep(64);
+    }
+    store_release_i(slot, 4 * t + q);
+  }
+  atomicAdd(R.ctr + 16, parts);
+}
+
+// Lane 0 of an idle worker: a ready part of the highest non-empty ring
+// (>= 0), a new request to activate (-4 - record index), -1 to stop, or -3.
+__device__ int serve_try_lane0(const KParams& p, unsigned long long deadline) {
+  if (load_relaxed_flag(&p.st->abort)) return -1;
+  for (int r = 0; r < 3; ++r) {
+    const ServeRing& R = p.sv.ring[r];
+    const int h = claim(R.ctr + 16, R.ctr + 8);
+    if (h >= 0) {
+      int* slot = R.slots + ((unsigned)h & R.mask);
+      const int v = wait_slot(p, slot, gtimer());
+      if (v >= 0) cuda::atomic_ref<int, cuda::thread_scope_device>(*slot).store(-1, cuda::memory_order_relaxed);
+      return v;
+    }
+  }
+  const int seen = load_relaxed_flag(p.sv.inbox_seen);
+  if (seen < load_acquire_sys(&p.sv.ctl->inbox_count)) {
+    if (atomicCAS(p.sv.inbox_seen, seen, seen + 1) == seen) return -4 - seen;
+    return -3;
+  }
+  if (load_acquire_sys(&p.sv.ctl->stop)) return -1;
+  if (gtimer() > deadline) {
+    raise_timeout(p, -2);
+    return -1;
+  }
+  return -3;
+}
+
+// Warp 0: activate inbox record `idx`: its value parameters, then its root
+// tasks into the rings (lanes in parallel).
+__device__ void serve_activate(const KParams& p, int idx) {
+  const int lane = threadIdx.x & 31;
+  const ServeRec* rec = &p.sv.ctl->inbox[idx % kServeInbox];
+  int slot = 0, root0 = 0, nroots = 0;
+  if (lane == 0) {
+    const volatile ServeRec* vr = rec;
+    slot = vr->slot;
+    root0 = vr->root0;
+    nroots = vr->nroots;
+    p.sv.req_param[2 * slot] = vr->rho;
+    p.sv.req_param[2 * slot + 1] = vr->tau;
+    p.sv.req_seq[slot] = vr->seq;
+    __threadfence();
+  }
+  root0 = __shfl_sync(0xffffffffu, root0, 0);
+  nroots = __shfl_sync(0xffffffffu, nroots, 0);
+  __syncwarp();
+  for (int i = lane; i < nroots; i += 32) push_task(p, __ldcg(p.sv.roots + root0 + i));
+}
+
+__device__ int serve_pop(const KParams& p, unsigned long long deadline) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int r = -3;
+    if (lane == 0) r = serve_try_lane0(p, deadline);
+    r = __shfl_sync(FULL, r, 0);
+    if (r >= -1) return r;
+    if (r <= -4) {
+      serve_activate(p, -4 - r);
+      continue;
+    }
+    __nanosleep(400);
+  }
+}
+
 // Lane 0: abort / budget check, then one attempt on the urgent queue.
 // Returns an item (>= 0), -1 to stop, or -3 when no urgent part is ready.
 __device__ int pop_urgent_lane0(const KParams& p, unsigned long long start) {
@@ -148,7 +266,8 @@ __device__ int pop_urgent_lane0(const KParams& p, unsigned long long start) {
 // 4 * task + part, or -1 when every part has been popped, the launch was
 // aborted, or the wait budget of this call expired (TIMEOUT; checked on
 // every pass of the loop).
-__device__ int pop_task(const KParams& p) {
+__device__ int pop_task(const KParams& p, unsigned long long deadline) {
+  if (p.serve) return serve_pop(p, deadline);
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int nb = p.nbuckets, ngroups = (nb + 31) / 32, nsuper = (ngroups + 31) / 32;
@@ -219,13 +338,51 @@ __device__ int pop_task(const KParams& p) {
 // successors whose last predecessor this was.
 __device__ void complete_task(const KParams& p, int t) {
   const int lane = threadIdx.x & 31;
-  const int s0 = p.succ_off[t], s1 = p.succ_off[t + 1];
+  const int s0 = __ldcg(p.succ_off + t), s1 = __ldcg(p.succ_off + t + 1);
   for (int q = s0 + lane; q < s1; q += 32) {
-    const int s = p.succ[q];
+    const int s = __ldcg(p.succ + q);
     STILES_CHECK(s >= 0 && s < p.ntasks, 6, t, 0);
     const int left = cuda::atomic_ref<int, cuda::thread_scope_device>(p.q.rem[s]).fetch_sub(1, cuda::memory_order_acq_rel);
     if (left == 1) push_task(p, s);
   }
+  if (p.serve) {  // request accounting: the last task of a request signals the host
+    __syncwarp();
+    if (lane == 0) {
+      const int slot = __ldcg(p.sv.treq + t);
+      if (atomicSub(p.sv.req_left + slot, 1) == 1) {
+        __threadfence_system();
+        store_release_sys(&p.sv.ctl->done_seq[slot], __ldcg(p.sv.req_seq + slot));
+      }
+    }
+  }
+}
+
+// OP_PREP (request server): tile column of A from the shape's base values and
+// the request's (rho, tau): band entries x rho, arrow entries unchanged,
+// diagonal tau + rho rb[i] + ra[i]. Every output element is written once.
+__device__ void run_prep(const KParams& p, const Task& tk, int t) {
+  const int slot = __ldcg(p.sv.treq + t);
+  const double rho = __ldcg(p.sv.req_param + 2 * slot), tau = __ldcg(p.sv.req_param + 2 * slot + 1);
+  double* O = resolve(p, tk.out);
+  const double* B = resolve(p, tk.cin);
+  const double* rb = resolve(p, tk.aux);
+  const double* ra = rb + tk.gcol;
+  const int b = tk.ldo, a = tk.ldc;
+  if (tk.flags & TF_CORNER) {  // arrow x arrow: entries unchanged, diagonal rebuilt
+    for (int e = threadIdx.x; e < a * a; e += NTHREADS) {
+      const int r = e % a, c = e / a;
+      O[e] = r == c ? tau + rho * rb[r] + ra[r] : __ldg(B + e);
+    }
+    return;
+  }
+  const int64_t bb = (int64_t)b * b, band = (1 + (int64_t)tk.ldx) * bb;
+  for (int64_t e = threadIdx.x; e < band; e += NTHREADS) {  // diagonal tile, then the sub-diagonal tiles
+    const int r = (int)(e % b);
+    const bool dg = e < bb && r == (int)(e / b);
+    O[e] = dg ? tau + rho * rb[r] + ra[r] : rho * __ldg(B + e);
+  }
+  const int64_t arrow0 = (1 + (int64_t)tk.zrows) * bb;  // the arrow tile (a x b) is copied
+  for (int64_t e = threadIdx.x; e < (int64_t)a * b; e += NTHREADS) O[arrow0 + e] = __ldg(B + arrow0 + e);
 }
 
 // Sub-tile of a task's output block computed by one part (rows r0 .. r0+rm,
@@ -270,7 +427,7 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
   for (int s = 0; s < tk.nseg; ++s) {
-    const Seg g = p.segs[tk.seg0 + s];
+    const Seg g = load_seg(p, tk.seg0 + s);
     const bool ta = g.trans & 1, tb = g.trans & 2;
     // op(A)[r0 + i, k] and op(B)[k, c0 + j]
     const double* A = resolve(p, g.a) + (ta ? (int64_t)sb.r0 * g.lda : (int64_t)sb.r0);
@@ -353,7 +510,7 @@ __device__ __forceinline__ void accumulate_f32(const KParams& p, const Task& tk,
 #pragma unroll
     for (int j = 0; j < TN; ++j) f[i][j] = 0.0f;
   for (int s = 0; s < tk.nseg; ++s) {
-    const Seg g = p.segs[tk.seg0 + s];
+    const Seg g = load_seg(p, tk.seg0 + s);
     const bool ta = g.trans & 1, tb = g.trans & 2;
     const double* A = resolve(p, g.a) + (ta ? (int64_t)sb.r0 * g.lda : (int64_t)sb.r0);
     const double* B = resolve(p, g.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * g.ldb);
@@ -513,7 +670,7 @@ __device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) res[j][q] = 0.0;
   for (int s = 0; s < tk.nseg; ++s) {
-    const Seg gs = p.segs[tk.seg0 + s];
+    const Seg gs = load_seg(p, tk.seg0 + s);
     const bool ta = gs.trans & 1, tb = gs.trans & 2;
     const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
     const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
@@ -973,7 +1130,7 @@ __device__ bool task_part_ok(const KParams& p, const Task& tk, const Sub& sb) {
   const int r0 = sb.r0, c0 = sb.c0, r1 = sb.r0 + sb.rm - 1, c1 = sb.c0 + sb.cn - 1;
   if (tk.m < 1 || tk.n < 1 || tk.m > FB || tk.n > FB || tk.op > OP_SYMUPD) return false;
   for (int s = 0; s < tk.nseg; ++s) {
-    const Seg g = p.segs[tk.seg0 + s];
+    const Seg g = load_seg(p, tk.seg0 + s);
     const int64_t amax = (g.trans & 1) ? (g.k - 1) + (int64_t)r1 * g.lda : r1 + (int64_t)(g.k - 1) * g.lda;
     const int64_t amin = (g.trans & 1) ? (int64_t)r0 * g.lda : r0;
     const int64_t bmax = (g.trans & 2) ? c1 + (int64_t)(g.k - 1) * g.ldb : (g.k - 1) + (int64_t)c1 * g.ldb;
@@ -995,6 +1152,10 @@ __device__ bool task_part_ok(const KParams& p, const Task& tk, const Sub& sb) {
 #endif
 
 __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double* smem) {
+  if (tk.op == OP_PREP) {
+    run_prep(p, tk, t);
+    return;
+  }
   const Sub sb = sub_of(tk, q);
   if (sb.rm <= 0 || sb.cn <= 0) return;
 #ifdef STILES_CHECKED
@@ -1022,11 +1183,13 @@ __device__ __forceinline__ unsigned smid() {
 __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
   extern __shared__ double smem[];
   __shared__ int s_item, s_last;
+  // request server: idle workers give up this long after the kernel started
+  const unsigned long long deadline = p.serve ? gtimer() + p.sv.deadline : 0ull;
   for (;;) {
     unsigned long long t_claim = 0;
     if (threadIdx.x < 32) {
       if (p.trace && threadIdx.x == 0) t_claim = gtimer();
-      const int v = pop_task(p);
+      const int v = pop_task(p, deadline);
       if (threadIdx.x == 0) s_item = v;
     }
     __syncthreads();
@@ -1034,7 +1197,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
     if (v < 0) break;
     const int t = v >> 2, q = v & 3;
 #ifdef STILES_CHECKED
-    if (t >= p.ntasks || q >= p.tasks[t].parts) {
+    if (t >= p.ntasks || q >= load_task(p, t).parts) {
       if (threadIdx.x == 0) check_fail(p, 8, t, q);
       break;
     }
@@ -1042,7 +1205,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
     unsigned long long t_ready = 0;
     if (p.trace && threadIdx.x == 0) t_ready = gtimer();
     __threadfence();
-    const Task tk = p.tasks[t];
+    const Task tk = load_task(p, t);
     run_task(p, tk, t, q, smem);
     __threadfence();
     __syncthreads();

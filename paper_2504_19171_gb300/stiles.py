@@ -31,6 +31,7 @@ STILES_ERR_OOM = -5
 STILES_ERR_UNSUPPORTED = -6
 STILES_ERR_PLAN = -7
 STILES_ERR_TOO_LARGE = -8
+STILES_ERR_BUSY = -9
 NOALLOC_SCRATCH_BYTES = 64 << 20
 STILES_FP64 = 0
 STILES_EMU64 = 1
@@ -49,6 +50,10 @@ EXPORTS = [
     "stiles_batch_create", "stiles_batch_offsets", "stiles_batch_workspace_bytes", "stiles_batch_factor_selinv",
     "stiles_batch_status", "stiles_batch_logdet", "stiles_batch_set_option", "stiles_batch_stats",
     "stiles_batch_destroy", "stiles_debug_validate_batch", "stiles_create_tuned",
+    "stiles_server_create", "stiles_server_shape_doubles", "stiles_server_set_base", "stiles_server_start",
+    "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
+    "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
+    "stiles_debug_validate_serve",
 ]
 
 
@@ -85,6 +90,19 @@ def _load() -> ctypes.CDLL:
         "stiles_factor_selinv_host": [vp, vp, vp, vp, vp, vp, vp, vp],
         "stiles_batch_create": [i32, P(i32), P(i32), P(i32), P(i32), i32, P(i32), P(vp)],
         "stiles_create_tuned": [i32, i32, i32, i32, i32, i32, P(vp)],
+        "stiles_server_create": [i32, P(i32), P(i32), P(i32), P(i32), i32, P(i32), sz, i32, P(vp)],
+        "stiles_server_shape_doubles": [vp, i32, P(sz), P(sz)],
+        "stiles_server_set_base": [vp, i32, vp, vp, vp],
+        "stiles_server_start": [vp, ctypes.c_double],
+        "stiles_server_submit": [vp, i32, ctypes.c_double, ctypes.c_double, i64, P(i32)],
+        "stiles_server_poll": [vp, i32, P(i32), P(i64), P(i32)],
+        "stiles_server_result": [vp, i32, P(i32), P(i64), P(ctypes.c_double)],
+        "stiles_server_sigma": [vp, i32, vp, P(vp)],
+        "stiles_server_release": [vp, i32],
+        "stiles_server_request_bytes": [vp, i32, P(sz)],
+        "stiles_server_stop": [vp],
+        "stiles_server_destroy": [vp],
+        "stiles_debug_validate_serve": [i32, i32, i32, i32, i32, i32],
         "stiles_batch_offsets": [vp, P(sz)],
         "stiles_batch_workspace_bytes": [vp, P(sz), P(sz)],
         "stiles_batch_factor_selinv": [vp, vp, vp, vp, vp, vp],
@@ -493,6 +511,106 @@ class StilesBatch:
     def close(self) -> None:
         if getattr(self, "h", None):
             stiles_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------- server -----
+def stiles_debug_validate_serve(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64,
+                                tuning: int = 0) -> int:
+    return _lib.stiles_debug_validate_serve(nt, b, band, arrow, precision, tuning)
+
+
+class StilesServer:
+    """Request server with continuous batching (see the C header). Shapes
+    (nt, b, band, arrow) form the pool; every shape needs a base matrix
+    (set_base) before start(). submit() admits a request (tau, rho) of a pool
+    shape or returns None when memory / slots are full; poll() returns the
+    completed (request, tag) pairs; result() / sigma() read them; release()
+    frees them."""
+
+    def __init__(self, shapes, data_bytes: int, max_requests: int = 64, precision: int = STILES_FP64,
+                 tuning=None, device: str = "cuda"):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("stiles needs a CUDA device (no CPU fallback)")
+        self.torch = torch
+        self.device = torch.device(device)
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        cols = list(zip(*self.shapes))
+        h = ctypes.c_void_p()
+        tun = _ivec(tuning) if tuning is not None else None
+        with torch.cuda.device(self.device):
+            _check(_lib.stiles_server_create(len(self.shapes), _ivec(cols[0]), _ivec(cols[1]), _ivec(cols[2]),
+                                             _ivec(cols[3]), precision, tun, int(data_bytes), max_requests,
+                                             ctypes.byref(h)), "stiles_server_create")
+        self.h = h.value
+        self.max_requests = max_requests
+        self.layouts = [PackedLayout(*sh) for sh in self.shapes]
+        self._req = (ctypes.c_int * max_requests)()
+        self._tag = (ctypes.c_longlong * max_requests)()
+
+    def shape_doubles(self, shape: int) -> Tuple[int, int]:
+        d, n = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.stiles_server_shape_doubles(self.h, shape, ctypes.byref(d), ctypes.byref(n)), "shape_doubles")
+        return d.value, n.value
+
+    def request_bytes(self, shape: int) -> int:
+        v = ctypes.c_size_t()
+        _check(_lib.stiles_server_request_bytes(self.h, shape, ctypes.byref(v)), "request_bytes")
+        return v.value
+
+    def set_base(self, shape: int, base, rb, ra) -> None:
+        """base / rb / ra: contiguous float64 torch tensors (host or device)."""
+        _check(_lib.stiles_server_set_base(self.h, shape, base.data_ptr(), rb.data_ptr(), ra.data_ptr()),
+               "stiles_server_set_base")
+
+    def start(self, window_s: float) -> None:
+        _check(_lib.stiles_server_start(self.h, float(window_s)), "stiles_server_start")
+
+    def submit(self, shape: int, tau: float, rho: float, tag: int = 0):
+        r = ctypes.c_int()
+        rc = _lib.stiles_server_submit(self.h, shape, float(tau), float(rho), int(tag), ctypes.byref(r))
+        if rc == STILES_ERR_BUSY:
+            return None
+        _check(rc, "stiles_server_submit")
+        return r.value
+
+    def poll(self):
+        n = ctypes.c_int()
+        _check(_lib.stiles_server_poll(self.h, self.max_requests, self._req, self._tag, ctypes.byref(n)),
+               "stiles_server_poll")
+        return [(self._req[i], self._tag[i]) for i in range(n.value)]
+
+    def result(self, request: int) -> Tuple[int, int, float]:
+        code, info, ld = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_double()
+        _check(_lib.stiles_server_result(self.h, request, ctypes.byref(code), ctypes.byref(info), ctypes.byref(ld)),
+               "stiles_server_result")
+        return code.value, info.value, ld.value
+
+    def sigma(self, request: int, out=None):
+        """Sigma of a completed request into `out` (float64 tensor, host or
+        device; allocated on the host if None) in its shape's packed layout."""
+        if out is None:
+            raise ValueError("pass an output tensor of the shape's packed size")
+        _check(_lib.stiles_server_sigma(self.h, request, out.data_ptr(), None), "stiles_server_sigma")
+        return out
+
+    def release(self, request: int) -> None:
+        _check(_lib.stiles_server_release(self.h, request), "stiles_server_release")
+
+    def stop(self) -> int:
+        return _lib.stiles_server_stop(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _lib.stiles_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

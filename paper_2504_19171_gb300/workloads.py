@@ -29,6 +29,9 @@ Recipes (all use ``numpy.random.default_rng(seed)``):
 * :func:`random_arrowhead_packed` -- the :func:`random_arrowhead` recipe
   drawn on a torch device straight into the packed band+arrow layout (for
   batches of many large matrices; its random stream is torch's, not numpy's).
+* :func:`sweep_base`, :func:`sweep_base_packed` -- the fixed part of a sweep
+  shape (base values and band / arrow absolute row sums) for the request
+  server, on the host or drawn on a torch device.
 """
 from __future__ import annotations
 
@@ -240,6 +243,29 @@ def sweep_arrowhead(nt: int, b: int, w: int, a: int, tau: float, rho: float, see
     return M
 
 
+def sweep_base(nt: int, b: int, w: int, a: int, seed: int = 0):
+    """The fixed part of a sweep shape, as a request server takes it: the base
+    matrix of :func:`sweep_arrowhead` (off-diagonal values, zero diagonal)
+    and its band / arrow absolute row sums ``rb``, ``ra`` over the full
+    symmetric matrix, so that request (tau, rho) is band x rho, arrow as is,
+    diagonal tau + rho rb + ra."""
+    base = random_arrowhead(nt, b, w, a, seed=seed)
+    M = ArrowheadTiles(nt, b, w, a)
+    rb, ra = np.zeros(M.n), np.zeros(M.n)
+    for (i, k), T in base.tiles.items():
+        T = T.copy()
+        if i == k:
+            np.fill_diagonal(T, 0.0)
+        M.tiles[(i, k)] = T
+        acc = ra if (i == nt) else rb
+        r0, c0 = M.row_start(i), M.row_start(k)
+        absT = np.abs(T)
+        acc[r0:r0 + T.shape[0]] += absT.sum(axis=1)
+        if i != k:
+            acc[c0:c0 + T.shape[1]] += absT.sum(axis=0)
+    return M, rb, ra
+
+
 def ar1_tridiagonal(n: int, rho: float) -> ArrowheadTiles:
     """Scalar AR(1) precision as a b = 1, w = 1, a = 0 arrowhead."""
     return ArrowheadTiles.from_dense(ar1_precision(n, rho), n, 1, 1, 0)
@@ -320,3 +346,44 @@ def random_arrowhead_packed(nt: int, b: int, w: int, a: int, seed: int, out, sca
     for i in range(nt + (1 if a > 0 else 0)):
         r = rows(i)
         view(i, i).diagonal().copy_(1.0 + rowabs[start(i):start(i) + r])
+
+
+def sweep_base_packed(nt: int, b: int, w: int, a: int, seed: int, out, scale: float = 0.1):
+    """Base matrix of a sweep shape drawn on a torch device into ``out`` (the
+    packed layout, as :func:`random_arrowhead_packed`): off-diagonal entries
+    N(0,1)*scale, zero diagonal. Returns (rb, ra): the band and arrow absolute
+    row sums over the full symmetric matrix (float64 tensors of length n on
+    ``out``'s device)."""
+    import torch
+
+    w = min(w, nt - 1)
+    dev = out.device
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    colstride = (1 + w) * b * b + a * b
+    n = nt * b + a
+    rb = torch.zeros(n, dtype=torch.float64, device=dev)
+    ra = torch.zeros(n, dtype=torch.float64, device=dev)
+    for k in range(nt + (1 if a > 0 else 0)):
+        rows_k = a if k == nt else b
+        tiles = [(k, k)] if k == nt else ([(k, k)] + [(i, k) for i in range(k + 1, min(k + w, nt - 1) + 1)] +
+                                          ([(nt, k)] if a > 0 else []))
+        for i, kk in tiles:
+            r = a if i == nt else b
+            if kk == nt:
+                off = nt * colstride
+            elif i == nt:
+                off = kk * colstride + (1 + w) * b * b
+            else:
+                off = kk * colstride + (i - kk) * b * b
+            T = torch.randn((r, rows_k), generator=gen, dtype=torch.float64, device=dev) * scale
+            if i == kk:
+                T = torch.tril(T, -1)
+                T = T + T.t()
+            acc = ra if i == nt else rb
+            absT = T.abs()
+            acc[i * b:i * b + r] += absT.sum(dim=1)
+            if i != kk:
+                acc[kk * b:kk * b + rows_k] += absT.sum(dim=0)
+            out[off:off + r * rows_k].view(rows_k, r).t().copy_(T)
+    return rb, ra

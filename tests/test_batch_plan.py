@@ -40,3 +40,12 @@ def test_invalid_tuning_codes_are_rejected():
         assert S.stiles_debug_validate(7, 64, 1, 8, S.PLAN_FUSED + 256 * tune) == S.STILES_ERR_INVALID_ARG
     assert S.stiles_debug_validate_batch([(4, 64, 1, 8)], 0, [12]) == S.STILES_ERR_INVALID_ARG
     assert S.stiles_debug_validate_batch([(4, 64, 1, 8), (5, 30, 2, 3)], 0, [3, 8 + 16]) == S.STILES_OK
+
+
+@pytest.mark.parametrize("shape", [(6, 64, 1, 16), (5, 100, 2, 37), (9, 40, 3, 0), (1, 50, 0, 5), (4, 3, 1, 2)])
+@pytest.mark.parametrize("prec", [S.STILES_FP64, S.STILES_EMU64])
+def test_serve_template_validates(shape, prec):
+    """Request-server table: in bounds (the PREP tasks read the base values
+    and the row-sum vectors behind them), PREP tasks are the only roots."""
+    assert S.stiles_debug_validate_serve(*shape, prec, 0) == S.STILES_OK
+    assert S.stiles_debug_validate_serve(*shape, prec, 2 + 8 + 16) == S.STILES_OK

@@ -31,3 +31,31 @@ def test_packed_generator_is_spd_and_dominant(shape):
     y = torch.full_like(x, float("nan"))
     W.random_arrowhead_packed(nt, b, w, a, 7, y)
     assert torch.equal(torch.nan_to_num(x, 123.0), torch.nan_to_num(y, 123.0))
+
+
+def test_sweep_base_packed_row_sums():
+    """rb / ra are the band / arrow absolute row sums of the packed base, so a
+    request (tau, rho) is strictly diagonally dominant."""
+    torch = pytest.importorskip("torch")
+    nt, b, w, a = 4, 5, 2, 3
+    colstride = (1 + w) * b * b + a * b
+    x = torch.zeros(nt * colstride + a * a, dtype=torch.float64)
+    rb, ra = W.sweep_base_packed(nt, b, w, a, 3, x)
+    M = W.ArrowheadTiles(nt, b, w, a)
+    flat = x.numpy()
+    for i, k in M.pattern():
+        r, c = M.rows(i), M.rows(k)
+        off = nt * colstride if k == nt else (k * colstride + (1 + w) * b * b if i == nt else k * colstride + (i - k) * b * b)
+        M.tiles[(i, k)] = flat[off:off + r * c].reshape(c, r).T.copy()
+    D = M.to_dense()
+    assert np.all(np.diag(D) == 0) and np.array_equal(D, D.T)
+    n = nt * b + a
+    band = np.zeros_like(D)
+    band[:nt * b, :nt * b] = D[:nt * b, :nt * b]
+    arrow = D - band
+    assert np.allclose(np.abs(band).sum(axis=1), rb.numpy())
+    assert np.allclose(np.abs(arrow).sum(axis=1), ra.numpy())
+    tau, rho = 0.5, 0.7
+    A = rho * band + arrow
+    A[np.diag_indices(n)] = tau + rho * rb.numpy() + ra.numpy()
+    assert np.linalg.eigvalsh(A).min() > 0
