@@ -500,8 +500,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.set_device(local)
     dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
     torch.cuda.set_device(dev)
-    nt, b, w, a = args.nt, WORKLOAD["b"], WORKLOAD["w"], WORKLOAD["a"]
-    M = W.spatiotemporal(nt=nt, side=32, a=a, rho=0.9, tau=WORKLOAD["tau"], seed=WORKLOAD["seed"])
+    nt, b, w, a = args.nt, WORKLOAD["b"], args.band, WORKLOAD["a"]
+    M = W.spatiotemporal(nt=nt, side=32, a=a, rho=0.9, tau=WORKLOAD["tau"], seed=WORKLOAD["seed"], band_power=w)
     st = S.Stiles(nt, b, w, a, device=str(dev))
     A_host = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).pin_memory()
     del M
@@ -566,7 +566,8 @@ def run_ours(args, world, rank, local):
             if "ms_per_step" in v:
                 v["speedup_vs_fp64"] = (1e3 * t_max / args.steps) / v["ms_per_step"]
     sha = kernel_sources_sha()
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha"] == sha else None
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha"] == sha and args.band == WORKLOAD["w"] and \
+        args.nt == WORKLOAD["nt"] else None
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -588,6 +589,10 @@ def run_ours(args, world, rank, local):
                      "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 pipe; tcgen05 has no f64 kind)"},
     }
     st.close()
+    if args.band != WORKLOAD["w"]:
+        line["config"]["workload"] += f"_band{args.band}"
+        line["config"]["w"] = args.band
+        line["config"]["Q_t"] = f"AR(1) precision to the power {args.band}, rho=0.9"
     if args.nt != WORKLOAD["nt"]:
         line["config"]["workload"] += f"_nt{args.nt}_profiling_case"
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
@@ -611,6 +616,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the EMU64 / FP32X lines")
     ap.add_argument("--variant-steps", type=int, default=2)
+    ap.add_argument("--band", type=int, default=WORKLOAD["w"],
+                    help="tile bandwidth: Q_t is replaced by Q_t^band (default 1; 4 raises the arithmetic intensity)")
     ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],
                     help="tile columns (default 200; smaller values are profiling cases, not bench lines)")
     ap.add_argument("--workload", default="spatiotemporal", choices=["spatiotemporal", "batched", "serving"],

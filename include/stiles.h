@@ -121,6 +121,18 @@ int stiles_create(int nt, int b, int band, int arrow, int precision, stiles_t *o
  * Other codes return STILES_ERR_INVALID_ARG. */
 int stiles_create_tuned(int nt, int b, int band, int arrow, int precision, int tuning, stiles_t *out);
 
+/* General selections (Sec. III-B, Fig. 2). Sigma tile (j, i) depends only on
+ * Sigma of tile columns after i (the recurrences of Sec. III-A run from the
+ * last column backwards), so any set of requested entries (r, c) of Sigma is
+ * served by computing tile columns >= first_column = min over the set of
+ * min(r, c) / b (arrow rows and columns: tile nt); those columns' phase-1 and
+ * phase-2 tasks are all that is kept (the factorization is always complete).
+ * This handle computes Sigma on L's pattern for tile columns >= first_column
+ * and writes no Sigma tile of earlier columns. 0 <= first_column <= nt (< nt
+ * without an arrow). The full inverse (Fig. 2 case 6) is the pattern with
+ * band = nt - 1: pack the tiles outside A's own band as zeros. */
+int stiles_create_selected(int nt, int b, int band, int arrow, int precision, int first_column, stiles_t *out);
+
 /* Doubles of one packed A / L / Sigma buffer (see the layout above). */
 int stiles_layout_doubles(stiles_t h, size_t *doubles);
 
@@ -232,7 +244,8 @@ int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size
 /* Plan statistics for a shape, computed on the host (no GPU, no handle).
  * which: 0 = factor plan, 1 = selinv plan, 2 = fused plan, plus 16 x the
  * stiles_precision of the plan (e.g. 2 + 16 * STILES_EMU64), plus 256 x a
- * tuning code (stiles_create_tuned); workers = number
+ * tuning code (stiles_create_tuned), plus 65536 x a first selected column
+ * (stiles_create_selected); workers = number
  * of persistent workers the list schedule assumes (e.g. the SM count).
  * stats[0] tasks, [1] segments, [2] waits, [3] counters,
  * [4] algorithmic flops of the tile operations (POTRF, TRTRI, LAUUM m^3/3;

@@ -394,8 +394,11 @@ struct Builder {
         for (int c = 0; c < R; ++c) s_col.push_back(newctr(false));
       }
     }
-    for (int i = 0; i < cols; ++i) emit_phase1(i);
-    for (int i = cols - 1; i >= 0; --i) emit_phase2(i);
+    // Sigma of tile column i depends only on Sigma of the columns after it and
+    // on column i's own phase 1: a selection starting at column sel0 needs
+    // exactly the phase-1 and phase-2 work of columns >= sel0.
+    for (int i = s.sel0; i < cols; ++i) emit_phase1(i);
+    for (int i = cols - 1; i >= s.sel0; --i) emit_phase2(i);
   }
 
   int32_t linv_ctr(int i, int c) const { return linv_col[linv_base[i] + c]; }
@@ -698,7 +701,7 @@ double tile_flops(const Shape& s, PlanKind kind) {
         for (size_t u = 0; u < t; ++u) f += 2.0 * mi * L.rows(st[u]) * mk;  // GEMM
       }
     }
-    if (kind != PLAN_FACTOR) {
+    if (kind != PLAN_FACTOR && k >= s.sel0) {
       f += 2.0 * mk * mk * mk / 3.0;                    // TRTRI + LAUUM
       for (int j : st) {
         const double mj = L.rows(j);
@@ -719,7 +722,8 @@ static double task_estimate(const Shape& s) {
 }
 
 static bool shape_ok(const Shape& s) {
-  return s.nt >= 1 && s.b >= 1 && s.w >= 0 && s.a >= 0 && s.w <= s.nt - 1 && tune_valid(s.tune);
+  return s.nt >= 1 && s.b >= 1 && s.w >= 0 && s.a >= 0 && s.w <= s.nt - 1 && tune_valid(s.tune) && s.sel0 >= 0 &&
+         s.sel0 <= (s.a > 0 ? s.nt : s.nt - 1);
 }
 
 int build_plan(const Shape& s, PlanKind kind, int workers, Plan* out) {

@@ -128,6 +128,7 @@ struct Shape {
   int nt, b, w, a;  // w already clipped to nt-1
   int prec = PREC_FP64;  // precision of the off-diagonal bulk products (Precision)
   int tune = 0;          // tuning code (see above)
+  int sel0 = 0;          // selected inversion of tile columns >= sel0 only (their phase 1 and 2)
 };
 
 // Dynamic schedule: a task becomes ready when its last predecessor finishes

@@ -104,18 +104,32 @@ static void free_handle(stiles_handle* h) {
   delete h;
 }
 
+static int create_handle(int nt, int b, int band, int arrow, int precision, int tuning, int first_column,
+                         stiles_t* out);
+
 extern "C" int stiles_create(int nt, int b, int band, int arrow, int precision, stiles_t* out) {
-  return stiles_create_tuned(nt, b, band, arrow, precision, 0, out);
+  return create_handle(nt, b, band, arrow, precision, 0, 0, out);
 }
 
 extern "C" int stiles_create_tuned(int nt, int b, int band, int arrow, int precision, int tuning, stiles_t* out) {
+  return create_handle(nt, b, band, arrow, precision, tuning, 0, out);
+}
+
+extern "C" int stiles_create_selected(int nt, int b, int band, int arrow, int precision, int first_column,
+                                      stiles_t* out) {
+  return create_handle(nt, b, band, arrow, precision, 0, first_column, out);
+}
+
+static int create_handle(int nt, int b, int band, int arrow, int precision, int tuning, int first_column,
+                         stiles_t* out) {
   if (!out) return STILES_ERR_INVALID_ARG;
   *out = nullptr;
   if (nt < 1 || b < 1 || band < 0 || arrow < 0 || !tune_valid(tuning)) return STILES_ERR_INVALID_ARG;
+  if (first_column < 0 || first_column > (arrow > 0 ? nt : nt - 1)) return STILES_ERR_INVALID_ARG;
   if (precision != STILES_FP64 && precision != STILES_EMU64 && precision != STILES_FP32X) return STILES_ERR_UNSUPPORTED;
   stiles_handle* h = new (std::nothrow) stiles_handle();
   if (!h) return STILES_ERR_OOM;
-  h->s = Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision, tuning};
+  h->s = Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision, tuning, first_column};
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;
@@ -367,12 +381,13 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
 }
 
 extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]) {
-  const int kind = which & 15, prec = (which >> 4) & 15, tune = which >> 8;
+  const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
   if (!stats || kind < 0 || kind > 2 || prec > PREC_FP32X || workers < 1 || !tune_valid(tune))
     return STILES_ERR_INVALID_ARG;
   if (nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
   Plan p;
-  int rc = build_plan(Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune}, (PlanKind)kind, workers, &p);
+  int rc = build_plan(Shape{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune, sel0}, (PlanKind)kind, workers,
+                      &p);
   if (rc) return rc;
   stats[0] = (long long)p.tasks.size();
   stats[1] = (long long)p.segs.size();
@@ -386,10 +401,10 @@ extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, 
 }
 
 extern "C" int stiles_debug_validate(int nt, int b, int band, int arrow, int which) {
-  const int kind = which & 15, prec = (which >> 4) & 15, tune = which >> 8;
+  const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
   if (kind < 0 || kind > 2 || prec > PREC_FP32X || !tune_valid(tune) || nt < 1 || b < 1 || band < 0 || arrow < 0)
     return STILES_ERR_INVALID_ARG;
-  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune};
+  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune, sel0};
   Plan p;
   int rc = build_plan(sh, (PlanKind)kind, 304, &p);
   return rc ? rc : validate_plan(p, sh, kind);

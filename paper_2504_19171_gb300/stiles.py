@@ -53,7 +53,7 @@ EXPORTS = [
     "stiles_server_create", "stiles_server_shape_doubles", "stiles_server_set_base", "stiles_server_start",
     "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
-    "stiles_debug_validate_serve",
+    "stiles_debug_validate_serve", "stiles_create_selected",
 ]
 
 
@@ -103,6 +103,7 @@ def _load() -> ctypes.CDLL:
         "stiles_server_stop": [vp],
         "stiles_server_destroy": [vp],
         "stiles_debug_validate_serve": [i32, i32, i32, i32, i32, i32],
+        "stiles_create_selected": [i32, i32, i32, i32, i32, i32, P(vp)],
         "stiles_batch_offsets": [vp, P(sz)],
         "stiles_batch_workspace_bytes": [vp, P(sz), P(sz)],
         "stiles_batch_factor_selinv": [vp, vp, vp, vp, vp, vp],
@@ -133,9 +134,15 @@ def _check(rc: int, what: str) -> None:
 
 
 # ----------------------------------------------------------- C names -----
-def stiles_create(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64, tuning: int = 0) -> int:
+def stiles_create(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64, tuning: int = 0,
+                  first_column: int = 0) -> int:
     h = ctypes.c_void_p()
-    if tuning:
+    if first_column:
+        if tuning:
+            raise ValueError("a selected plan takes the default tuning")
+        _check(_lib.stiles_create_selected(nt, b, band, arrow, precision, first_column, ctypes.byref(h)),
+               "stiles_create_selected")
+    elif tuning:
         _check(_lib.stiles_create_tuned(nt, b, band, arrow, precision, tuning, ctypes.byref(h)), "stiles_create_tuned")
     else:
         _check(_lib.stiles_create(nt, b, band, arrow, precision, ctypes.byref(h)), "stiles_create")
@@ -360,7 +367,7 @@ class Stiles:
     """One handle plus its device buffers (torch float64 tensors on CUDA)."""
 
     def __init__(self, nt: int, b: int, band: int, arrow: int, device: str = "cuda", wait_budget_s: float = None,
-                 precision: int = STILES_FP64, tuning: int = 0):
+                 precision: int = STILES_FP64, tuning: int = 0, first_column: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -368,7 +375,7 @@ class Stiles:
         self.torch = torch
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
-            self.h = stiles_create(nt, b, band, arrow, precision, tuning)
+            self.h = stiles_create(nt, b, band, arrow, precision, tuning, first_column)
         self.layout = PackedLayout(nt, b, band, arrow)
         self.nt, self.b, self.w, self.a = nt, b, self.layout.w, arrow
         Lb, Sb, Wb = stiles_workspace_bytes(self.h)
@@ -618,3 +625,24 @@ class StilesServer:
             self.close()
         except Exception:
             pass
+
+
+def first_column_for(entries, nt: int, b: int) -> int:
+    """Symbolic pruning of a selection: the first tile column whose Sigma a
+    set of requested entries (r, c) of Sigma needs (entries of the arrow rows /
+    columns map to tile nt). Pass the result as ``first_column``."""
+    cols = [min(min(int(r), int(c)) // b, nt) for r, c in entries]
+    if not cols:
+        raise ValueError("empty selection")
+    return min(cols)
+
+
+def widen_band(M, w_full: int = None):
+    """The same matrix with its tile band widened (default: every tile, the
+    full inverse of Fig. 2 case 6): tiles outside the original band are zero."""
+    from .workloads import ArrowheadTiles
+    w_full = M.nt - 1 if w_full is None else w_full
+    out = ArrowheadTiles(M.nt, M.b, w_full, M.a)
+    for i, k in out.pattern():
+        out.tiles[(i, k)] = M.tiles[(i, k)].copy() if (i, k) in M.tiles else np.zeros((out.rows(i), out.rows(k)))
+    return out
