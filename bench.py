@@ -411,7 +411,7 @@ def run_serving(args, world, rank, local):
         """arrivals: times (s) or None for the closed loop; returns stats."""
         srv.start(window + 120.0)
         queue, start_t, lat, done_flops, done_n, failed = [], {}, [], 0.0, 0, 0
-        tag = 0
+        admitted, offered_n, not_admitted = 0, 0, 0
         t_start = time.perf_counter()
         in_flight = 0
         nxt = 0
@@ -421,6 +421,7 @@ def run_serving(args, world, rank, local):
                 while nxt < len(arrivals) and arrivals[nxt] <= now and arrivals[nxt] < window:
                     queue.append((nxt, arrivals[nxt]))
                     nxt += 1
+                    offered_n += 1
             else:
                 while now < window and in_flight + len(queue) < closed_conc:
                     queue.append((nxt, now))
@@ -434,6 +435,7 @@ def run_serving(args, world, rank, local):
                 queue.pop(0)
                 start_t[i] = (t_arr, shape)
                 in_flight += 1
+                admitted += 1
             for r, i in srv.poll():
                 t_arr, shape = start_t.pop(i)
                 code = srv.result(r)[0]
@@ -445,15 +447,17 @@ def run_serving(args, world, rank, local):
                 done_n += 1
                 done_flops += flops[shape]
                 lat.append(time.perf_counter() - t_start - t_arr)
-            if now >= window and (arrivals is None or True):
+            if now >= window:
+                not_admitted += len(queue)  # offered in the window, never admitted (memory full)
+                queue.clear()
                 if in_flight == 0 or now > window + 100.0:
                     break
-                queue.clear()  # arrivals after the window are not offered
             time.sleep(0.0005)
         elapsed = time.perf_counter() - t_start
         status = srv.stop()
         lat_ms = np.array(lat) * 1e3
-        return {"completed": done_n, "failed": failed, "left_unadmitted_at_window_end": len(queue),
+        return {"completed": done_n, "failed": failed, "admitted": admitted, "not_admitted": not_admitted,
+                "offered": offered_n if arrivals is not None else admitted,
                 "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
                 "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
                 "served_tflops": done_flops / elapsed / 1e12, "requests_per_s": done_n / elapsed,

@@ -401,12 +401,18 @@ int stiles_server_poll(stiles_server_t h, int max, int *requests, long long *tag
 int stiles_server_result(stiles_server_t h, int request, int *code, long long *info, double *logdet);
 
 /* Sigma of a completed request (packed layout of its shape): copied to
- * host_out (host or device memory) if not NULL, and/or its device address in
- * *device_ptr (valid until the request is released). */
+ * host_out (host memory while the server runs: a device-side copy could need
+ * an SM, which the running kernel holds) if not NULL, and/or its device
+ * address in *device_ptr (valid until the request is released). */
 int stiles_server_sigma(stiles_server_t h, int request, double *host_out, const double **device_ptr);
 
 /* Free a completed request's memory, tables and slot. */
 int stiles_server_release(stiles_server_t h, int request);
+
+/* Status of the server kernel read while it runs: *code STILES_OK, or
+ * STILES_ERR_TIMEOUT once a wait (or the window) expired; *info the first
+ * error's detail; *tasks_done tasks completed since the start. */
+int stiles_server_status(stiles_server_t h, int *code, long long *info, long long *tasks_done);
 
 /* Data-arena bytes a request of `shape` takes. */
 int stiles_server_request_bytes(stiles_server_t h, int shape, size_t *bytes);

@@ -8,7 +8,8 @@
 // others run therefore share the GPU task by task (continuous batching). The
 // last task of a request writes the request's sequence number to host-mapped
 // memory; the host reads the results with copies on a second stream while the
-// kernel keeps running.
+// kernel keeps running. While the kernel runs, every transfer is a plain
+// host<->device copy (copy engine): nothing may need an SM.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -254,8 +255,9 @@ extern "C" int stiles_server_create(int nshapes, const int* nt, const int* b, co
     rc = STILES_ERR_OOM;
   if (!rc && cudaHostGetDevicePointer((void**)&h->ctl_dev, h->ctl_host, 0) != cudaSuccess) rc = STILES_ERR_CUDA;
   if (!rc) {
-    h->stage_bytes = (size_t)max_tasks * (sizeof(Task) + 4 * sizeof(int32_t) + 4) + (size_t)max_segs * sizeof(Seg) +
-                     (size_t)max_succ * sizeof(int32_t) + (size_t)max_roots * sizeof(int32_t) + 4096;
+    h->stage_bytes = (size_t)max_tasks * (sizeof(Task) + 5 * sizeof(int32_t) + 4) + (size_t)max_segs * sizeof(Seg) +
+                     (size_t)max_succ * sizeof(int32_t) + (size_t)max_roots * sizeof(int32_t) +
+                     (size_t)max_diag * sizeof(int32_t) + 4096;
     if (cudaHostAlloc((void**)&h->stage, h->stage_bytes, cudaHostAllocDefault) != cudaSuccess) rc = STILES_ERR_OOM;
   }
   if (!rc && (cudaStreamCreateWithFlags(&h->kstream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -418,7 +420,13 @@ extern "C" int stiles_server_submit(stiles_server_t h, int shape, double tau, do
   st += sizeof(int32_t) * n;
   int32_t* rt = (int32_t*)st;
   st += sizeof(int32_t) * R.nr;
+  int32_t* zero = (int32_t*)st;  // pdone
+  st += sizeof(int32_t) * n;
+  int32_t* minus1 = (int32_t*)st;  // pivot slots
+  st += sizeof(int32_t) * R.nd;
   int32_t* left = (int32_t*)st;
+  memset(zero, 0, sizeof(int32_t) * n);
+  for (int64_t q = 0; q < R.nd; ++q) minus1[q] = -1;
   const int64_t base = T.base_off;
   for (int64_t t = 0; t < n; ++t) {
     Task x = P.tasks[t];
@@ -472,10 +480,14 @@ extern "C" int stiles_server_submit(stiles_server_t h, int shape, double tau, do
   cok = cok && cudaMemcpyAsync(h->succ_off + R.t0, so, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, cs) == cudaSuccess;
   if (R.ns) cok = cok && cudaMemcpyAsync(h->succ + R.s0, sc, sizeof(int32_t) * R.ns, cudaMemcpyHostToDevice, cs) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->rem + R.t0, rm, sizeof(int32_t) * n, cudaMemcpyHostToDevice, cs) == cudaSuccess;
-  cok = cok && cudaMemsetAsync(h->pdone + R.t0, 0, sizeof(int32_t) * n, cs) == cudaSuccess;
+  // copy-engine transfers only: a memset may run as a kernel, which would
+  // wait behind the running server kernel
+  cok = cok && cudaMemcpyAsync(h->pdone + R.t0, zero, sizeof(int32_t) * n, cudaMemcpyHostToDevice, cs) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->treq + R.t0, tq, sizeof(int32_t) * n, cudaMemcpyHostToDevice, cs) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->roots + R.r0, rt, sizeof(int32_t) * R.nr, cudaMemcpyHostToDevice, cs) == cudaSuccess;
-  if (R.nd) cok = cok && cudaMemsetAsync(h->badpiv + R.d0, 0xff, sizeof(int32_t) * R.nd, cs) == cudaSuccess;
+  if (R.nd)
+    cok = cok && cudaMemcpyAsync(h->badpiv + R.d0, minus1, sizeof(int32_t) * R.nd, cudaMemcpyHostToDevice, cs) ==
+                     cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->req_left + slot, left, sizeof(int32_t), cudaMemcpyHostToDevice, cs) == cudaSuccess;
   cok = cok && cudaStreamSynchronize(cs) == cudaSuccess;
   if (!cok) return STILES_ERR_CUDA;
@@ -586,6 +598,22 @@ extern "C" int stiles_server_release(stiles_server_t h, int request) {
 extern "C" int stiles_server_request_bytes(stiles_server_t h, int shape, size_t* bytes) {
   if (!h || !bytes || shape < 0 || shape >= (int)h->shapes.size()) return STILES_ERR_INVALID_ARG;
   *bytes = 3 * (size_t)((h->shapes[shape].doubles + 31) / 32 * 32) * sizeof(double);
+  return STILES_OK;
+}
+
+// Device status of the running (or last) server kernel, read without
+// waiting for it: code (STILES_OK / STILES_ERR_TIMEOUT / STILES_ERR_PLAN),
+// info of the first error, tasks completed so far.
+extern "C" int stiles_server_status(stiles_server_t h, int* code, long long* info, long long* tasks_done) {
+  if (!h) return STILES_ERR_INVALID_ARG;
+  DevStatus ds;
+  if (cudaSetDevice(h->device) != cudaSuccess ||
+      cudaMemcpyAsync(&ds, h->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->cstream) != cudaSuccess ||
+      cudaStreamSynchronize(h->cstream) != cudaSuccess)
+    return STILES_ERR_CUDA;
+  if (code) *code = ds.code == STILES_DEV_TIMEOUT ? STILES_ERR_TIMEOUT : ds.code == STILES_DEV_CHECK ? STILES_ERR_PLAN : STILES_OK;
+  if (info) *info = (long long)ds.info;
+  if (tasks_done) *tasks_done = (long long)ds.done;
   return STILES_OK;
 }
 

@@ -53,7 +53,7 @@ EXPORTS = [
     "stiles_server_create", "stiles_server_shape_doubles", "stiles_server_set_base", "stiles_server_start",
     "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
-    "stiles_debug_validate_serve", "stiles_create_selected",
+    "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status",
 ]
 
 
@@ -104,6 +104,7 @@ def _load() -> ctypes.CDLL:
         "stiles_server_destroy": [vp],
         "stiles_debug_validate_serve": [i32, i32, i32, i32, i32, i32],
         "stiles_create_selected": [i32, i32, i32, i32, i32, i32, P(vp)],
+        "stiles_server_status": [vp, P(i32), P(i64), P(i64)],
         "stiles_batch_offsets": [vp, P(sz)],
         "stiles_batch_workspace_bytes": [vp, P(sz), P(sz)],
         "stiles_batch_factor_selinv": [vp, vp, vp, vp, vp, vp],
@@ -611,6 +612,12 @@ class StilesServer:
 
     def release(self, request: int) -> None:
         _check(_lib.stiles_server_release(self.h, request), "stiles_server_release")
+
+    def status(self) -> Tuple[int, int, int]:
+        code, info, done = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(_lib.stiles_server_status(self.h, ctypes.byref(code), ctypes.byref(info), ctypes.byref(done)),
+               "stiles_server_status")
+        return code.value, info.value, done.value
 
     def stop(self) -> int:
         return _lib.stiles_server_stop(self.h)
