@@ -188,7 +188,8 @@ def measure_variants(S, st, stream, dev, flops, logdet64, args):
     S64 = st.S
     smax = float(S64.abs().max().item())
     for name, prec in (("emu64", S.STILES_EMU64), ("fp32x", S.STILES_FP32X)):
-        sv = S.Stiles(st.nt, st.b, st.w, st.a, device=str(dev), precision=prec)
+        tune = args.tuner.best(st.b, st.w, st.a, prec) if args.tuner else 0
+        sv = S.Stiles(st.nt, st.b, st.w, st.a, device=str(dev), precision=prec, tuning=tune)
         sv.A = st.A
         sv.factor_selinv(stream)
         torch.cuda.synchronize(dev)
@@ -207,6 +208,7 @@ def measure_variants(S, st, stream, dev, flops, logdet64, args):
         ld = sv.logdet()
         err = float((sv.S - S64).abs().max().item()) / smax
         out[name] = {"value": flops / t / 1e12, "unit": "TFLOP/s (FP64-equivalent flops)", "ms_per_step": 1e3 * t,
+                     "tuning": tune,
                      "steps": args.variant_steps, "speedup_vs_fp64": None,
                      "sigma_err_vs_fp64": err, "logdet_rel_err_vs_fp64": abs(ld - logdet64) / abs(logdet64)}
         sv.A = None
@@ -506,7 +508,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(dev)
     nt, b, w, a = args.nt, WORKLOAD["b"], args.band, WORKLOAD["a"]
     M = W.spatiotemporal(nt=nt, side=32, a=a, rho=0.9, tau=WORKLOAD["tau"], seed=WORKLOAD["seed"], band_power=w)
-    st = S.Stiles(nt, b, w, a, device=str(dev))
+    from paper_2504_19171_gb300 import autotune as AT
+    tuner = None if args.no_autotune else AT.Autotuner(AT.default_cache_path())
+    tune64 = tuner.best(b, w, a, S.STILES_FP64) if tuner else 0
+    st = S.Stiles(nt, b, w, a, device=str(dev), tuning=tune64)
     A_host = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).pin_memory()
     del M
     st.A = A_host.to(dev)
@@ -562,6 +567,7 @@ def run_ours(args, world, rank, local):
         te = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
         e2e_value = whole_job_rate(world, e2e_steps, flops, te) / 1e12
 
+    args.tuner = tuner
     variants = None if args.no_variants else measure_variants(S, st, stream, dev, flops, logdet, args)
 
     achieved = flops / (sum(per_launch) / len(per_launch)) / 1e12
@@ -579,7 +585,7 @@ def run_ours(args, world, rank, local):
         "config": dict(WORKLOAD, nt=nt, n=nt * b + a, parallelism=f"replicas{world}" if world > 1 else "single",
                        flops_per_step=flops, flop_convention="tile ops: POTRF/TRTRI/LAUUM m^3/3, TRSM/TRMM m k^2, "
                        "SYRK and symmetric Sigma_ii update m^2 k, GEMM 2mnk",
-                       l2="inputs larger than L2 (A, L, Sigma 3.45 GB each; L2 129 MB)"),
+                       l2="inputs larger than L2 (A, L, Sigma 3.45 GB each; L2 129 MB)", tuning=tune64),
         "matrices_per_s": whole_job_rate(world, args.steps, 1.0, t_max),
         "logdet": logdet,
         "clocks": clk,
