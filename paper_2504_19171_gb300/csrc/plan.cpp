@@ -19,8 +19,11 @@
 // (every b x b POTRF/TRSM/SYRK/GEMM decomposes exactly into FB-block POTRF,
 // TRSM and GEMM updates), which keeps the critical path at about three small
 // block operations per FB columns. Updates into one block are applied by a
-// chain of tasks (increasing source column); the last update of a diagonal
-// block is fused into its POTRF.
+// chain of tasks in increasing source column, so a block's terms are always
+// summed in the same order whatever the schedule (bit-reproducible results).
+// Batches (build_batch_plan) merge several matrices' tables under one list
+// schedule; request-server templates (build_serve_template) add one OP_PREP
+// task per tile column that builds A on the device.
 #include "plan.h"
 
 #include <algorithm>
@@ -578,8 +581,6 @@ struct Builder {
       blevel[t] = cost[t] + best;
       cp = std::max(cp, blevel[t]);
     }
-    std::vector<double> tlevel(nt_, 0.0);
-    (void)tlevel;
     // list schedule: free workers take the ready task with the largest bottom level
     using RItem = std::pair<double, int32_t>;
     std::priority_queue<RItem> ready;

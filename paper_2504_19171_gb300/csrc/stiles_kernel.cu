@@ -1,20 +1,26 @@
-// Persistent dependency-driven FP64 kernel for tiled Cholesky and two-phase
+// Persistent dependency-driven kernel for tiled Cholesky and two-phase
 // selected inversion on GB300 (sm_103a).
 //
-// Two CTAs per SM (each 4 warps) claim tasks in the planner's list-schedule order with an
-// atomic counter, waits (bounded by %globaltimer) until the counters its task
-// depends on reach their targets, runs the task, then signals. A task only
-// waits on tasks claimed before it, by CTAs that are already running, so the
-// claim order cannot deadlock whatever the number of resident CTAs. These
-// counters play the role of the producer/consumer flags of Algorithm 3
-// ("WaitForTile / SignalTileReady"), kept on the device.
+// Two CTAs per SM (each 4 warps) run task parts until every part of the plan
+// has been executed. A task becomes ready when its last predecessor finishes
+// (per-task predecessor counters, decremented by the finishing task: the
+// device form of Algorithm 3's "WaitForTile / SignalTileReady" flags); the
+// finisher pushes its parts into a queue, and idle workers claim parts with
+// fetch-and-add on availability counters. Static plans queue parts in
+// buckets of the host's list-schedule order behind an urgent FIFO for the
+// factorization's frontier; the request server (serve mode) uses three FIFO
+// rings and activates new requests from a host-mapped inbox while it runs.
+// Every wait is bounded by %globaltimer and ends the launch with a TIMEOUT
+// status instead of hanging.
 //
 // FP64 has no tensor-core path on GB300 (tcgen05 has no f64 kind), so the
-// block products run on the FP64 FMA pipe: 2 DFMA per clock per SM, reached
-// with 4 warps. Each task stages FB x KC panels of its operands in shared
-// memory (L2-only loads, so data published by other SMs is never read from a
-// stale L1 line) and accumulates a 64 x 64 block in registers (4 x 8 per
-// thread).
+// FP64 block products run on the FP64 FMA pipe: 2 DFMA per clock per SM,
+// reached with 4 warps. Each task stages FB x KC panels of its operands in
+// shared memory (L2-only loads, so data published by other SMs is never read
+// from a stale L1 line) and accumulates up to a 64 x 64 block in registers
+// (4 x 8 per thread). The reduced-precision modes replace the products of
+// the bulk tasks: emulated FP64 (bf16 digit products on the tensor cores)
+// and FP32-class (FP32 FMA).
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
