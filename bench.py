@@ -143,6 +143,35 @@ def whole_job_rate(world: int, steps: int, units_per_step: float, t_max: float) 
     return world * steps * units_per_step / t_max
 
 
+def host_info() -> dict:
+    """The host cores the CPU oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and model is None:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
+def oracle_n1040_seconds() -> float:
+    """The CPU oracle on the n = 1040 configuration (16 tiles of 64, band 1,
+    arrow 16, seed 0), single thread, best of 3."""
+    from oracle import oracle as O
+    from paper_2504_19171_gb300 import workloads as W
+    M = W.random_arrowhead(16, 64, 1, 16, seed=0)
+    best = float("inf")
+    for _ in range(3):
+        t0 = time.perf_counter()
+        O.selinv(M)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
 def oracle_sample(nt_sample: int):
     """Run the CPU oracle on the first nt_sample tile columns of the workload
     family; returns (seconds, flops)."""
@@ -177,7 +206,8 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(WORKLOAD, sample_nt=SAMPLE_NT),
             "matrices_per_s": args.steps / total * SAMPLE_NT / WORKLOAD["nt"],
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -616,7 +646,8 @@ def run_ours(args, world, rank, local):
         dt, f = oracle_sample(SAMPLE_NT)
         line["cpu_baseline"] = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {SAMPLE_NT} tile columns + arrow of the same matrix family "
-                                          f"(n = {SAMPLE_NT * 1024 + 64}, {f / 1e9:.2f} GFLOP) in {dt:.1f} s"}
+                                          f"(n = {SAMPLE_NT * 1024 + 64}, {f / 1e9:.2f} GFLOP) in {dt:.1f} s",
+                                "host": host_info(), "n1040_seconds_best_of_3": oracle_n1040_seconds()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
