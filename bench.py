@@ -547,7 +547,7 @@ def run_ours(args, world, rank, local):
     # is a batch of short matrices (the batched / served regime), whose best code
     # (26 for b = 1024) makes this single long matrix 21 % slower.
     tuner = None
-    tune64 = 0
+    tune64 = args.tuning
     st = S.Stiles(nt, b, w, a, device=str(dev), tuning=tune64)
     A_host = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).pin_memory()
     del M
@@ -676,6 +676,7 @@ def main():
     ap.add_argument("--serve-gb", type=float, default=120.0, help="serving: data arena (GiB)")
     ap.add_argument("--serve-concurrency", type=int, default=16, help="serving: requests in flight (closed loop)")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default tuning codes")
+    ap.add_argument("--tuning", type=int, default=0, help="spatiotemporal: plan tuning code (stiles_create_tuned)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
