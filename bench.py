@@ -506,8 +506,12 @@ def run_serving(args, world, rank, local):
     open_loop = run_phase(list(arr), reqs, args.serve_window)
     open_loop["offered_tflops"] = offered / 1e12
     open_loop["offered_requests_per_s"] = float(np.sum(arr < args.serve_window)) / args.serve_window
-    closed = run_phase(None, reqs, args.serve_window, closed_conc=args.serve_concurrency)
-    closed["concurrency"] = args.serve_concurrency
+    closed_runs = []
+    for conc in [int(c) for c in str(args.serve_concurrency).split(",")]:
+        r = run_phase(None, reqs, args.serve_window, closed_conc=conc)
+        r["concurrency"] = conc
+        closed_runs.append(r)
+    closed = max(closed_runs, key=lambda r: r["requests_per_s"])
     srv.close()
     line = {
         "metric": "served selected-inversion requests: p50/p99 latency and throughput",
@@ -516,7 +520,7 @@ def run_serving(args, world, rank, local):
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": dict(SERVE, window_s=args.serve_window, data_arena_gb=args.serve_gb,
                        parallelism=f"replicas{world}" if world > 1 else "single"),
-        "open_loop": open_loop, "closed_loop": closed, "setup_s": setup_s,
+        "open_loop": open_loop, "closed_loop": closed, "closed_loop_runs": closed_runs, "setup_s": setup_s,
         "e2e": None, "gpu_launches": 2,
     }
     if rank == 0:
@@ -674,7 +678,8 @@ def main():
     ap.add_argument("--precision", default="emu64", choices=["fp64", "emu64", "fp32x"], help="serving precision")
     ap.add_argument("--serve-window", type=float, default=30.0, help="serving: seconds of arrivals per phase")
     ap.add_argument("--serve-gb", type=float, default=120.0, help="serving: data arena (GiB)")
-    ap.add_argument("--serve-concurrency", type=int, default=16, help="serving: requests in flight (closed loop)")
+    ap.add_argument("--serve-concurrency", default="1,16",
+                    help="serving: requests in flight in the closed loops (comma list; 1 = unloaded latency)")
     ap.add_argument("--no-autotune", action="store_true", help="batched: default tuning codes")
     ap.add_argument("--tuning", type=int, default=0, help="spatiotemporal: plan tuning code (stiles_create_tuned)")
     args = ap.parse_args()

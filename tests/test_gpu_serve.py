@@ -121,3 +121,26 @@ def test_serve_admission_by_memory():
         assert srv.stop() == S.STILES_OK
     finally:
         srv.close()
+
+
+@pytest.mark.gpu
+def test_serve_emulated_fp64():
+    """Served requests in the emulated-FP64 mode against the oracle (the
+    emulated mode's 1e-12 target)."""
+    S = need_gpu()
+    srv = _server(S, precision=S.STILES_EMU64)
+    try:
+        reqs = [(0, 0.9, 0.8), (1, 2.0, 0.6), (2, 0.5, 0.95)]
+        for tag, (shape, tau, rho) in enumerate(reqs):
+            assert srv.submit(shape, tau, rho, tag=tag) is not None
+        done = _wait(srv, len(reqs))
+        for tag, (shape, tau, rho) in enumerate(reqs):
+            r = done[tag]
+            assert srv.result(r)[0] == S.STILES_OK
+            A = W.sweep_arrowhead(*POOL[shape], tau, rho, seed=20 + shape)
+            _, Sr, _ = O.selinv(A)
+            assert rel_err(_sigma(srv, r, shape), Sr) < 1e-12
+            srv.release(r)
+        assert srv.stop() == S.STILES_OK
+    finally:
+        srv.close()
