@@ -600,9 +600,12 @@ def run_ours(args, world, rank, local):
         st.factor_selinv_host(A_host, S_host, stream)  # one untimed pass to settle the copy path
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_wall = []
         e0.record(stream)
         for _ in range(e2e_steps):
+            tw = time.perf_counter()
             st.factor_selinv_host(A_host, S_host, stream)
+            e2e_wall.append(1e3 * (time.perf_counter() - tw))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         te = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
@@ -631,6 +634,7 @@ def run_ours(args, world, rank, local):
         "logdet": logdet,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_host.numel() * 8),
+                "step_wall_ms": None if args.no_e2e else [round(v, 1) for v in e2e_wall],
                 "d2h_bytes_per_step": int(S_host.numel() * 8 + 8)},
         "gpu_launches": args.steps * (2 if not args.no_e2e else 1),
         "variants": variants,
