@@ -374,6 +374,21 @@ def run_batched(args, world, rank, local):
         st.close()
     t_solo = max_over_ranks(t_solo, world)
     fp = results["fp64"]
+    cpu = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        # the oracle on the draw's smallest matrix (host values of the same recipe), scaled to the draw's flops
+        from oracle import oracle as O
+        m_small = min(range(count), key=lambda m: S.stiles_plan_stats(*shapes[m], S.PLAN_FUSED, 152)["flops"])
+        sh = shapes[m_small]
+        f_small = S.stiles_plan_stats(*sh, S.PLAN_FUSED, 152)["flops"]
+        M = W.random_arrowhead(*sh, seed=1000 + m_small)
+        t0 = time.perf_counter()
+        O.selinv(M)
+        dt = time.perf_counter() - t0
+        rate = f_small / dt
+        cpu = {"value": rate / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"the draw's smallest matrix {sh} ({f_small / 1e9:.2f} GFLOP) in {dt:.1f} s",
+               "matrices_per_s_scaled": rate / (fp["flops_per_batch"] / count), "host": host_info()}
     line = {
         "metric": "batched factor+selinv matrices/s (FP64; EMU64 / FP32X variants; vs plain FP64 per-matrix)",
         "value": fp["matrices_per_s"], "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
@@ -388,6 +403,7 @@ def run_batched(args, world, rank, local):
                             "bitwise_equal_to_batch": f"{same}/{count}"},
         "variants": {k: v for k, v in results.items() if k != "fp64"},
         "fp64": fp,
+        "cpu_baseline": cpu,
         "roofline": {"bound": "alu", "achieved": fp["achieved_per_launch"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": fp["achieved_per_launch"] / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": "stiles::persistent_kernel (FP64 pipe)"},
