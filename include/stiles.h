@@ -393,6 +393,13 @@ int stiles_server_start(stiles_server_t h, double window_s);
  * no memory or slot is free now. */
 int stiles_server_submit(stiles_server_t h, int shape, double tau, double rho, long long tag, int *request);
 
+/* Admit a request of pool shape `shape` with explicit values: A_host (host
+ * memory, the shape's packed layout, stiles_server_shape_doubles doubles) is
+ * copied into the request's memory before it joins the kernel, instead of
+ * being built from the base matrix. Same results and errors as
+ * stiles_server_submit. */
+int stiles_server_submit_values(stiles_server_t h, int shape, const double *A_host, long long tag, int *request);
+
 /* Requests completed since the last poll, each reported once (up to max). */
 int stiles_server_poll(stiles_server_t h, int max, int *requests, long long *tags, int *n_out);
 

@@ -369,6 +369,7 @@ __device__ void complete_task(const KParams& p, int t) {
 __device__ void run_prep(const KParams& p, const Task& tk, int t) {
   const int slot = __ldcg(p.sv.treq + t);
   const double rho = __ldcg(p.sv.req_param + 2 * slot), tau = __ldcg(p.sv.req_param + 2 * slot + 1);
+  if (rho != rho) return;  // a request with explicit values: its A was copied into place
   double* O = resolve(p, tk.out);
   const double* B = resolve(p, tk.cin);
   const double* rb = resolve(p, tk.aux);

@@ -357,9 +357,27 @@ extern "C" int stiles_server_start(stiles_server_t h, double window_s) {
   return STILES_OK;
 }
 
+static int submit_impl(stiles_server_t h, int shape, double tau, double rho, const double* A_host, long long tag,
+                       int* request);
+
 // Admission and activation of one request (see the file comment).
 extern "C" int stiles_server_submit(stiles_server_t h, int shape, double tau, double rho, long long tag,
                                     int* request) {
+  if (!(rho == rho) || !(tau == tau)) return STILES_ERR_INVALID_ARG;
+  return submit_impl(h, shape, tau, rho, nullptr, tag, request);
+}
+
+// A request with explicit values: A_host (host memory, the shape's packed
+// layout) is copied into the request's L before activation, and its PREP
+// tasks leave it as it is (rho = NaN marks the request).
+extern "C" int stiles_server_submit_values(stiles_server_t h, int shape, const double* A_host, long long tag,
+                                           int* request) {
+  if (!A_host) return STILES_ERR_INVALID_ARG;
+  return submit_impl(h, shape, 0.0, __builtin_nan(""), A_host, tag, request);
+}
+
+static int submit_impl(stiles_server_t h, int shape, double tau, double rho, const double* A_host, long long tag,
+                       int* request) {
   if (!h || !request || shape < 0 || shape >= (int)h->shapes.size()) return STILES_ERR_INVALID_ARG;
   if (!h->running) return STILES_ERR_INVALID_ARG;
   const ShapeT& T = h->shapes[shape];
@@ -489,6 +507,9 @@ extern "C" int stiles_server_submit(stiles_server_t h, int shape, double tau, do
     cok = cok && cudaMemcpyAsync(h->badpiv + R.d0, minus1, sizeof(int32_t) * R.nd, cudaMemcpyHostToDevice, cs) ==
                      cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->req_left + slot, left, sizeof(int32_t), cudaMemcpyHostToDevice, cs) == cudaSuccess;
+  if (A_host)
+    cok = cok && cudaMemcpyAsync(h->data + R.dL, A_host, sizeof(double) * T.doubles, cudaMemcpyHostToDevice, cs) ==
+                     cudaSuccess;
   cok = cok && cudaStreamSynchronize(cs) == cudaSuccess;
   if (!cok) return STILES_ERR_CUDA;
   // publish the activation record (the kernel reads it after an acquire of inbox_count)

@@ -53,7 +53,7 @@ EXPORTS = [
     "stiles_server_create", "stiles_server_shape_doubles", "stiles_server_set_base", "stiles_server_start",
     "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
-    "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status",
+    "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status", "stiles_server_submit_values",
 ]
 
 
@@ -105,6 +105,7 @@ def _load() -> ctypes.CDLL:
         "stiles_debug_validate_serve": [i32, i32, i32, i32, i32, i32],
         "stiles_create_selected": [i32, i32, i32, i32, i32, i32, P(vp)],
         "stiles_server_status": [vp, P(i32), P(i64), P(i64)],
+        "stiles_server_submit_values": [vp, i32, vp, i64, P(i32)],
         "stiles_batch_offsets": [vp, P(sz)],
         "stiles_batch_workspace_bytes": [vp, P(sz), P(sz)],
         "stiles_batch_factor_selinv": [vp, vp, vp, vp, vp, vp],
@@ -588,6 +589,27 @@ class StilesServer:
         if rc == STILES_ERR_BUSY:
             return None
         _check(rc, "stiles_server_submit")
+        return r.value
+
+    def submit_values(self, shape: int, A_host, tag: int = 0):
+        """Admit a request with explicit values: A_host is a contiguous host
+        float64 tensor (or array) in the shape's packed layout."""
+        import numpy as _np
+        if isinstance(A_host, _np.ndarray):
+            if A_host.dtype != _np.float64 or not A_host.flags["C_CONTIGUOUS"]:
+                raise ValueError("A_host must be a contiguous float64 array")
+            ptr, size = A_host.ctypes.data, A_host.size
+        else:
+            if A_host.dtype != self.torch.float64 or A_host.device.type != "cpu" or not A_host.is_contiguous():
+                raise ValueError("A_host must be a contiguous CPU float64 tensor")
+            ptr, size = A_host.data_ptr(), A_host.numel()
+        if size != self.layouts[shape].doubles:
+            raise ValueError("A_host must hold the shape's packed layout")
+        r = ctypes.c_int()
+        rc = _lib.stiles_server_submit_values(self.h, shape, ptr, int(tag), ctypes.byref(r))
+        if rc == STILES_ERR_BUSY:
+            return None
+        _check(rc, "stiles_server_submit_values")
         return r.value
 
     def poll(self):

@@ -144,3 +144,29 @@ def test_serve_emulated_fp64():
         assert srv.stop() == S.STILES_OK
     finally:
         srv.close()
+
+
+@pytest.mark.gpu
+def test_serve_explicit_values():
+    """A request carrying its own A (copied in before it joins the kernel)
+    against the oracle, mixed with sweep requests."""
+    S = need_gpu()
+    srv = _server(S)
+    try:
+        A1 = W.random_arrowhead(*POOL[1], seed=77)
+        flat = srv.layouts[1].pack(A1.tiles, np.zeros(srv.layouts[1].doubles))
+        assert srv.submit(0, 1.2, 0.8, tag=0) is not None
+        assert srv.submit_values(1, flat, tag=1) is not None
+        assert srv.submit(2, 0.7, 0.9, tag=2) is not None
+        done = _wait(srv, 3)
+        r = done[1]
+        code, _, ld = srv.result(r)
+        assert code == S.STILES_OK
+        _, Sr, ldr = O.selinv(A1)
+        assert rel_err(_sigma(srv, r, 1), Sr) < FP64_TOL
+        assert abs(ld - ldr) < FP64_TOL * max(1.0, abs(ldr))
+        for q in done.values():
+            srv.release(q)
+        assert srv.stop() == S.STILES_OK
+    finally:
+        srv.close()
