@@ -46,7 +46,7 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
-TRAFFIC = {"sources_sha": "a6f11c9cb1e2bd06", "bytes_per_launch": 35.22e9}
+TRAFFIC = {"sources_sha": "5673e21dec1acf2c", "bytes_per_launch": 35.94e9}
 
 
 def kernel_sources_sha() -> str:

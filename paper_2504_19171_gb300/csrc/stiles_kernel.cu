@@ -906,76 +906,124 @@ __device__ __forceinline__ void trsm_cols_ln(double* X, const double* T, const d
   }
 }
 
+// Trailing rank-1 update of the block POTRF, one batch of B elements per
+// thread: element e of the packed lower triangle (width w, row pairs
+// (a, w-1-a) of w+1 elements) maps to X[c0+a][c0+b] and is updated by column
+// k. fetch() loads a batch (indices past ne are marked -1) and advances the
+// (i, kk) walk; apply() writes it.
+struct Rank1Walk {
+  int c0, w, w1, k, ne, nt, di, dk, i, kk;
+};
+template <int B>
+__device__ __forceinline__ void rank1_fetch(const double* X, Rank1Walk& s, int e, int (&id)[B], double (&xr)[B],
+                                            double (&lr)[B], double (&lc)[B]) {
+#pragma unroll
+  for (int u = 0; u < B; ++u) {
+    const int a = s.kk <= s.i ? s.i : s.w - 1 - s.i, b = s.kk <= s.i ? s.kk : s.kk - s.i - 1;
+    id[u] = e + u * s.nt < s.ne ? (s.c0 + a) * LDS + s.c0 + b : -1;
+    if (id[u] >= 0) {
+      xr[u] = X[id[u]];
+      lr[u] = X[(s.c0 + a) * LDS + s.k];
+      lc[u] = X[(s.c0 + b) * LDS + s.k];
+    }
+    s.kk += s.dk;
+    s.i += s.di;
+    if (s.kk >= s.w1) {
+      s.kk -= s.w1;
+      ++s.i;
+    }
+  }
+}
+template <int B>
+__device__ __forceinline__ void rank1_apply(double* X, const int (&id)[B], const double (&xr)[B],
+                                            const double (&lr)[B], const double (&lc)[B]) {
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+    if (id[u] >= 0) X[id[u]] = fma(-lr[u], lc[u], xr[u]);
+}
+
 // In-place lower Cholesky of the n x n block X (n <= FB), one column per
 // step with a two-column lookahead, so that a step has one block barrier:
 //   warp 0, step j: pivot d = X[j][j], r = rsqrt(d) (one dependent FP64
-//     chain instead of sqrt then a divide), L_jj = d r, column j scaled by r,
-//     then column j+1 updated by columns j-1 and j (it is pivot j+1 next);
-//   warps 1-3, step j: columns j+2 .. n-1 (lower part) updated by column j-1.
+//     chain instead of sqrt then a divide), column j scaled by r, then
+//     column j+1 updated by columns j-1 and j (it is pivot j+1 next); the
+//     column j-1 term does not depend on r and is applied while r is formed,
+//     lane 0's scaled row j+1 is broadcast by a shuffle;
+//   warps 1-3, step j: columns j+2 .. n-1 (lower part) updated by column j-1,
+//     walking the lower triangle of width w as w/2 row pairs (a, w-1-a) of
+//     w+1 elements each (no lane idles), in batches of six.
 // Every column thus receives the updates of the columns before it in
 // ascending order, and only warp 0's pivot chain is on the critical path.
-// The warps 1-3 rank-1 update walks the lower triangle of width w as w/2
-// row pairs (a, w-1-a) of w+1 elements each, so no lane idles.
+// X[j][j] keeps the pivot d until the end (nothing reads it after step j);
+// r is kept in the row's padding slot X[j][FB], and L_jj = d r and the pivot
+// check are done for all columns at once after the loop.
 // Returns the first column (0-based) whose pivot was not positive, or -1.
 __device__ int potrf_smem(double* X, int n) {
+  static_assert(FB <= 64 && LDS > FB, "two rows per lane of warp 0; a padding column per row");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int s_bad;
-  int bad = -1;
+  if (tid == 0) s_bad = n;
   for (int j = 0; j < n; ++j) {
     if (warp == 0) {
+      const int j1 = j + 1;
       const double d = X[j * LDS + j];
-      const double rr = rsqrt(d);
-      if (lane == 0) {
-        if (!(d > 0.0) && bad < 0) bad = j;
-        X[j * LDS + j] = d * rr;
-      }
-      for (int r = j + 1 + lane; r < n; r += 32) X[r * LDS + j] *= rr;
-      __syncwarp();
-      if (j + 1 < n) {
-        const int j1 = j + 1;
-        const double l1 = X[j1 * LDS + j];
-        const double l0 = j > 0 ? X[j1 * LDS + j - 1] : 0.0;
-        for (int r = j1 + lane; r < n; r += 32) {
-          double x = X[r * LDS + j1];
-          if (j > 0) x = fma(-X[r * LDS + j - 1], l0, x);
-          X[r * LDS + j1] = fma(-X[r * LDS + j], l1, x);
+      const double l0 = j > 0 && j1 < n ? X[j1 * LDS + j - 1] : 0.0;
+      double xj[2] = {0.0, 0.0}, x1[2] = {0.0, 0.0}, lj[2] = {0.0, 0.0};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = j1 + lane + 32 * u;
+        if (r < n) {
+          xj[u] = X[r * LDS + j];
+          x1[u] = X[r * LDS + j1];
+          if (j > 0) x1[u] = fma(-X[r * LDS + j - 1], l0, x1[u]);
         }
+      }
+      const double rr = rsqrt(d);
+      if (lane == 0) X[j * LDS + FB] = rr;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = j1 + lane + 32 * u;
+        if (r < n) {
+          lj[u] = xj[u] * rr;
+          X[r * LDS + j] = lj[u];
+        }
+      }
+      const double l1 = __shfl_sync(0xffffffffu, lj[0], 0);  // L[j+1][j], row j+1 is lane 0's
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int r = j1 + lane + 32 * u;
+        if (r < n) X[r * LDS + j1] = fma(-lj[u], l1, x1[u]);
       }
     } else if (j > 0 && j + 2 < n) {
-      const int c0 = j + 2, w = n - c0, w1 = w + 1, k = j - 1;
-      const int t = tid - 32, nt = NTHREADS - 32;
-      const int di = nt / w1, dk = nt % w1;
-      int i = t / w1, kk = t % w1;
+      Rank1Walk s;
+      s.c0 = j + 2;
+      s.w = n - s.c0;
+      s.w1 = s.w + 1;
+      s.k = j - 1;
+      s.ne = s.w * s.w1 / 2;
+      s.nt = NTHREADS - 32;
+      s.di = s.nt / s.w1;
+      s.dk = s.nt % s.w1;
+      const int t = tid - 32;
+      s.i = t / s.w1;
+      s.kk = t % s.w1;
       constexpr int B = 6;  // elements per batch: their loads are issued before their stores
-      for (int e = t; e < w * w1 / 2; e += B * nt) {
-        int idx[B];
-        double xr[B], lr[B], lc[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-          const int a = kk <= i ? i : w - 1 - i, b = kk <= i ? kk : kk - i - 1;
-          idx[u] = e + u * nt < w * w1 / 2 ? (c0 + a) * LDS + c0 + b : -1;
-          if (idx[u] >= 0) {
-            xr[u] = X[idx[u]];
-            lr[u] = X[(c0 + a) * LDS + k];
-            lc[u] = X[(c0 + b) * LDS + k];
-          }
-          kk += dk;
-          i += di;
-          if (kk >= w1) {
-            kk -= w1;
-            ++i;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < B; ++u)
-          if (idx[u] >= 0) X[idx[u]] = fma(-lr[u], lc[u], xr[u]);
+      int id[B];
+      double xr[B], lr[B], lc[B];
+      for (int e = t; e < s.ne; e += B * s.nt) {
+        rank1_fetch<B>(X, s, e, id, xr, lr, lc);
+        rank1_apply<B>(X, id, xr, lr, lc);
       }
     }
     __syncthreads();
   }
-  if (tid == 0) s_bad = bad;
+  if (tid < n) {
+    const double d = X[tid * LDS + tid];
+    if (!(d > 0.0)) atomicMin(&s_bad, tid);
+    X[tid * LDS + tid] = d * X[tid * LDS + FB];
+  }
   __syncthreads();
-  return s_bad;
+  return s_bad < n ? s_bad : -1;
 }
 
 template <int TM, int TN>
