@@ -167,15 +167,24 @@ int stiles_factor_selinv(stiles_t h, const double *A_tiles, double *L_tiles, dou
                          void *stream);
 
 /* End-to-end form of stiles_factor_selinv for callers whose matrix lives in
- * host memory: on `stream`, copy A_host (stiles_layout_doubles doubles, the
- * packed tile layout) into the device buffer A_dev, run the fused factor +
- * selected inversion into L_dev / Sigma_dev, and copy Sigma_dev back into
- * Sigma_host. Host buffers should be page-locked (cudaHostAlloc /
- * torch pin_memory) for the copies to be asynchronous; they must stay valid
- * until the stream reaches the end of the call. Device buffers follow the
- * rules of stiles_factor_selinv (A_dev may alias L_dev). Asynchronous: read
- * the status / logdet afterwards as usual. A_host and Sigma_host may be the
- * same buffer (the input is consumed before Sigma is written back). */
+ * host memory: A_host (stiles_layout_doubles doubles, the packed tile layout)
+ * in, Sigma_host (same layout) out, the fused factor + selected inversion in
+ * between, all on `stream`. Two ways, chosen per call:
+ *   - A_host and Sigma_host page-locked and mapped into the device's address
+ *     space (cudaHostAlloc, cudaHostRegister with cudaHostRegisterMapped, or
+ *     torch pin_memory on a unified-addressing system; each buffer inside one
+ *     such allocation) and not overlapping: the kernel reads each block of A
+ *     over the host link when its first factor task needs it, and writes
+ *     every final Sigma block to Sigma_host as well as to Sigma_dev, so both
+ *     transfers overlap the computation. A_dev is not used (not written).
+ *     Entries of Sigma_host outside the computed tiles keep their values.
+ *   - otherwise: copy A_host into A_dev, run the fused call, copy Sigma_dev
+ *     back into Sigma_host (page-locked buffers make the copies asynchronous;
+ *     A_host and Sigma_host may then be the same buffer).
+ * Host buffers must stay valid until the stream reaches the end of the call.
+ * Device buffers follow the rules of stiles_factor_selinv (A_dev may alias
+ * L_dev; Sigma_dev holds the full result in both ways). Asynchronous: read
+ * the status / logdet afterwards as usual. */
 int stiles_factor_selinv_host(stiles_t h, const double *A_host, double *Sigma_host, double *A_dev, double *L_dev,
                               double *Sigma_dev, void *scratch, void *stream);
 

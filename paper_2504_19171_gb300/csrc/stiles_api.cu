@@ -190,7 +190,8 @@ extern "C" int stiles_workspace_bytes(stiles_t h, size_t* L_bytes, size_t* sigma
   return STILES_OK;
 }
 
-static int launch(stiles_t h, int kind, const double* A, double* L, double* S, void* scratch, void* stream) {
+static int launch(stiles_t h, int kind, const double* A, double* L, double* S, void* scratch, void* stream,
+                  double* smirror = nullptr) {
   if (!h || !scratch) return STILES_ERR_INVALID_ARG;
   if (((uintptr_t)scratch) % 256 != 0) return STILES_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
@@ -220,6 +221,7 @@ static int launch(stiles_t h, int kind, const double* A, double* L, double* S, v
   p.buf[BUF_L] = L;
   p.buf[BUF_S] = S;
   p.buf[BUF_W] = (double*)scr;
+  p.smirror = smirror;
   p.budget_ns = h->budget_ns;
   p.trace = h->dtrace;
   if (h->dtrace && cudaMemsetAsync(h->dtrace, 0, 16 * sizeof(unsigned long long) * h->trace_tasks, st) != cudaSuccess)
@@ -249,6 +251,23 @@ extern "C" int stiles_factor_selinv(stiles_t h, const double* A, double* L, doub
   return launch(h, PLAN_FUSED, A, L, S, scratch, stream);
 }
 
+// Device address of the `bytes`-long host buffer at `ptr` when it is
+// page-locked and mapped into the current device's address space (both of
+// its ends resolve into one mapping), else null: pageable memory, device
+// memory, or a buffer that runs past its page-locked allocation.
+static const char* mapped_host(const void* ptr, size_t bytes) {
+  cudaPointerAttributes first{}, last{};
+  if (cudaPointerGetAttributes(&first, ptr) != cudaSuccess ||
+      cudaPointerGetAttributes(&last, (const char*)ptr + bytes - 1) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer is an answer here, not an error
+    return nullptr;
+  }
+  if (first.type != cudaMemoryTypeHost || last.type != cudaMemoryTypeHost || !first.devicePointer ||
+      (const char*)last.devicePointer != (const char*)first.devicePointer + bytes - 1)
+    return nullptr;
+  return (const char*)first.devicePointer;
+}
+
 extern "C" int stiles_factor_selinv_host(stiles_t h, const double* A_host, double* S_host, double* A_dev,
                                          double* L_dev, double* S_dev, void* scratch, void* stream) {
   if (!h || !A_host || !S_host || !A_dev || !L_dev || !S_dev || S_dev == L_dev || S_dev == A_dev ||
@@ -256,6 +275,16 @@ extern "C" int stiles_factor_selinv_host(stiles_t h, const double* A_host, doubl
     return STILES_ERR_INVALID_ARG;
   const size_t bytes = (size_t)Layout(h->s).doubles() * sizeof(double);
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
+  // Page-locked, separate host buffers: the kernel reads A over the host link
+  // as its factor tasks first need each block, and writes every final Sigma
+  // block to the host buffer as well as to S_dev, so both transfers overlap
+  // the computation instead of preceding and following it.
+  const double* A_map = (const double*)mapped_host(A_host, bytes);
+  double* S_map = (double*)mapped_host(S_host, bytes);
+  const char *a0 = (const char*)A_host, *s0 = (const char*)S_host;
+  const bool apart = a0 + bytes <= s0 || s0 + bytes <= a0;
+  if (A_map && S_map && apart) return launch(h, PLAN_FUSED, A_map, L_dev, S_dev, scratch, stream, S_map);
   if (cudaMemcpyAsync(A_dev, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STILES_ERR_CUDA;
   const int rc = launch(h, PLAN_FUSED, A_dev, L_dev, S_dev, scratch, stream);
   if (rc != STILES_OK) return rc;

@@ -118,6 +118,8 @@ struct KParams {
   DevStatus* st;        // status block (reset before the launch)
   double* logdet_part;  // one partial sum of log diag(L) per POTRF task
   double* buf[4];       // BUF_A, BUF_L, BUF_S, BUF_W base pointers
+  double* smirror;      // optional: second copy of every final Sigma write, same layout as buf[BUF_S]
+                        // (a host buffer mapped into the device's address space), or null
   long long budget_ns;  // bound of one dependency wait
   int32_t* badpiv;     // optional: per POTRF task, first failing pivot (0-based in its block) or -1
   unsigned long long* trace;  // optional: 4 words per task (claim, ready, end ns; sm/cta/op), or null

@@ -1051,6 +1051,8 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
     case OP_NEG: {
       double* O = resolve(p, tk.out) + sb.r0 + (int64_t)sb.c0 * tk.ldo;
       const double* C = tk.op == OP_UPD ? resolve(p, tk.cin) + sb.r0 + (int64_t)sb.c0 * tk.ldc : nullptr;
+      // an off-diagonal Sigma block is final when its NEG task writes it
+      double* Om = tk.op == OP_NEG && p.smirror ? p.smirror + (O - p.buf[BUF_S]) : nullptr;
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -1061,6 +1063,7 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
             if (tk.op == OP_UPD) v = __ldcg(C + r + (int64_t)c * tk.ldc) - v;
             else if (tk.op == OP_NEG) v = -v;
             O[r + (int64_t)c * tk.ldo] = v;
+            if (Om) Om[r + (int64_t)c * tk.ldo] = v;
           }
         }
       break;
@@ -1069,11 +1072,15 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
       acc_to_smem<TM, TN>(p, tk, sb, acc, X, true, 1.0);
       __syncthreads();
       double* O = resolve(p, tk.out);
+      // the diagonal tile's Sigma blocks are final when their SYMUPD writes them
       if ((tk.flags & TF_SYM_DIAG) && sb.r0 == sb.c0) {  // diagonal sub-block: keep its lower triangle, mirror it
         double* D = O + sb.r0 + (int64_t)sb.c0 * tk.ldo;
+        double* Dm = p.smirror ? p.smirror + (D - p.buf[BUF_S]) : nullptr;
         for (int e = tid; e < sb.rm * sb.cn; e += NTHREADS) {
           const int r = e % sb.rm, c = e / sb.rm;
-          D[r + (int64_t)c * tk.ldo] = r >= c ? X[r * LDS + c] : X[c * LDS + r];
+          const double v = r >= c ? X[r * LDS + c] : X[c * LDS + r];
+          D[r + (int64_t)c * tk.ldo] = v;
+          if (Dm) Dm[r + (int64_t)c * tk.ldo] = v;
         }
       } else {
         // this sub-block, and its transpose into the mirror position: inside the
@@ -1082,13 +1089,17 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
         const bool dblk = tk.flags & TF_SYM_DIAG;
         double* M = dblk ? O + sb.c0 + (int64_t)sb.r0 * tk.ldo : resolve(p, tk.aux) + sb.c0 + (int64_t)sb.r0 * tk.ldx;
         const int ldm = dblk ? tk.ldo : tk.ldx;
+        double* Dm = p.smirror ? p.smirror + (D - p.buf[BUF_S]) : nullptr;
+        double* Mm = p.smirror ? p.smirror + (M - p.buf[BUF_S]) : nullptr;
         for (int e = tid; e < sb.rm * sb.cn; e += NTHREADS) {
           const int r = e % sb.rm, c = e / sb.rm;
           D[r + (int64_t)c * tk.ldo] = X[r * LDS + c];
+          if (Dm) Dm[r + (int64_t)c * tk.ldo] = X[r * LDS + c];
         }
         for (int e = tid; e < sb.rm * sb.cn; e += NTHREADS) {
           const int c = e % sb.cn, r = e / sb.cn;
           M[c + (int64_t)r * ldm] = X[r * LDS + c];
+          if (Mm) Mm[c + (int64_t)r * ldm] = X[r * LDS + c];
         }
       }
       break;

@@ -413,9 +413,11 @@ class Stiles:
                              self.scratch.data_ptr(), self.stream_ptr(stream))
 
     def factor_selinv_host(self, A_host, S_host, stream=None) -> float:
-        """End-to-end call with host buffers: copy the packed A (pinned host
-        float64 tensor) to the device, factor and invert in one launch, copy
-        Sigma back into S_host (pinned) and return logdet (synchronizes)."""
+        """End-to-end call with host buffers (packed layout, CPU float64):
+        factor and invert A_host in one launch, Sigma into S_host, return
+        logdet (synchronizes). With two separate pinned tensors the kernel
+        reads A and writes Sigma over the host link while it computes;
+        otherwise the library copies A in before and Sigma out after."""
         torch = self.torch
         if self.A is None:
             self.A = torch.empty(self.doubles, dtype=torch.float64, device=self.device)

@@ -89,28 +89,41 @@ def test_bitwise_repeatable():
 
 
 @pytest.mark.gpu
-def test_host_buffer_entry_point():
-    """stiles_factor_selinv_host (H2D of A, launch, D2H of Sigma on one
-    stream) returns the same bits as the device-buffer call, and Sigma
-    matches the oracle."""
+@pytest.mark.parametrize("buffers", ["pinned", "pageable", "same_pinned"])
+def test_host_buffer_entry_point(buffers):
+    """stiles_factor_selinv_host returns the same bits as the device-buffer
+    call, and Sigma matches the oracle, in both of its ways: separate pinned
+    buffers (the kernel reads A and writes the final Sigma blocks over the
+    host link), and pageable or shared buffers (copies before and after)."""
     import torch
     M = W.random_arrowhead(9, 96, 2, 20, seed=21)
     _, S_dev, ld_dev, _ = run_gpu(M, "fused")
     S = need_gpu()
     st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=5.0)
     try:
-        A_host = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).pin_memory()
-        S_host = torch.full((st.doubles,), np.nan, dtype=torch.float64).pin_memory()
-        ld = st.factor_selinv_host(A_host, S_host)
-        assert st.status()[0] == S.STILES_OK
-        got = st.layout.unpack(S_host.numpy())
+        packed = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles)))
+        if buffers == "pinned":
+            A_host = packed.pin_memory()
+            S_host = torch.full((st.doubles,), np.nan, dtype=torch.float64).pin_memory()
+        elif buffers == "pageable":
+            A_host = packed.clone()
+            S_host = torch.full((st.doubles,), np.nan, dtype=torch.float64)
+        else:
+            A_host = S_host = packed.pin_memory()
+        for rep in range(2):  # a second call on the same handle and buffers
+            if buffers == "same_pinned" and rep:
+                A_host.copy_(packed)
+            ld = st.factor_selinv_host(A_host, S_host)
+            assert st.status()[0] == S.STILES_OK
+            got = st.layout.unpack(S_host.numpy())
+            for key in S_dev:
+                assert np.array_equal(got[key], S_dev[key]), (buffers, rep, key)
+            assert ld == ld_dev
     finally:
         st.close()
-    for key in S_dev:
-        assert np.array_equal(got[key], S_dev[key])
-    assert ld == ld_dev
     _, Sref, _ = O.selinv(M)
     assert rel_err(got, Sref) < FP64_TOL
+
 
 EMU_TOL = 1e-12  # emulated-FP64 target against the FP64 oracle
 PREC_SHAPES = [(16, 64, 1, 16), (5, 100, 2, 37), (9, 130, 1, 70), (4, 3, 1, 2), (7, 40, 4, 0), (12, 64, 3, 64)]
