@@ -678,6 +678,89 @@ def run_ours(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def run_selections(args, world, rank, local):
+    """Selected inversion: Sigma only where a request needs it. On the same
+    spatio-temporal matrix, time the FP64 factor + selected inversion for
+    requests whose earliest entry lies in tile column f (the plan keeps the
+    whole factorization and phase 1 / phase 2 of the columns >= f only):
+    f = 0 (every column), nt/2, and nt (the arrow block: the fixed effects'
+    covariance). Each selected run's tiles are compared with the full run's."""
+    import numpy as np
+    import torch
+
+    from paper_2504_19171_gb300 import build as B
+    B.build()
+    from paper_2504_19171_gb300 import stiles as S
+    from paper_2504_19171_gb300 import workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    nt, b, w, a = args.nt, WORKLOAD["b"], args.band, WORKLOAD["a"]
+    M = W.spatiotemporal(nt=nt, side=32, a=a, rho=0.9, tau=WORKLOAD["tau"], seed=WORKLOAD["seed"], band_power=w)
+    stream = torch.cuda.current_stream(dev)
+    A_dev = None
+    full_S = None
+    rows, clk = [], None
+    for f in (0, nt // 2, nt):
+        st = S.Stiles(nt, b, w, a, device=str(dev), first_column=f)
+        if A_dev is None:
+            A_dev = torch.from_numpy(st.layout.pack(M.tiles, np.zeros(st.doubles))).to(dev)
+            del M
+        st.A = A_dev
+        flops = S.stiles_plan_stats(nt, b, w, a, S.PLAN_FUSED + (f << 16), 152)["flops"]
+        for _ in range(args.warmup):
+            st.factor_selinv(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(dev.index if dev.index is not None else 0).start() if f == nt else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st.factor_selinv(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if sampler:
+            clk = sampler.stop()
+        code, info, _ = st.status()
+        if code != S.STILES_OK:
+            raise SystemExit(f"selection f={f}: {S.strerror(code)} info={info}")
+        t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        if f == 0:
+            full_S, full_t = st.S, t
+            same = None
+        else:  # every tile of the selected columns, bit for bit
+            lay = st.layout
+            same = all(torch.equal(st.S[o:o + lay.rows(i) * lay.rows(k)], full_S[o:o + lay.rows(i) * lay.rows(k)])
+                       for i, k in lay.pattern() if k >= f for o in [lay.offset(i, k)])
+        rows.append({"first_column": f, "ms_per_step": 1e3 * t / args.steps, "flops_per_step": flops,
+                     "tflops": whole_job_rate(world, args.steps, flops, t) / 1e12,
+                     "speedup_vs_full": full_t / t, "bitwise_equal_to_full": same})
+        if f != 0:
+            st.S = None
+        st.close()
+    last = rows[-1]
+    line = {
+        "metric": "factor + selected inversion ms per step (FP64), arrow-block selection", "value": last["ms_per_step"],
+        "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": last["ms_per_step"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, workload="spatiotemporal_selections", nt=nt, n=nt * b + a,
+                       parallelism=f"replicas{world}" if world > 1 else "single",
+                       selections="first tile column f = 0, nt/2, nt",
+                       l2="inputs larger than L2 (A, L, Sigma 3.45 GB each; L2 129 MB)"),
+        "selections": rows, "clocks": clk, "e2e": None, "gpu_launches": 3 * (args.steps + args.warmup),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -692,9 +775,10 @@ def main():
                     help="tile bandwidth: Q_t is replaced by Q_t^band (default 1; 4 raises the arithmetic intensity)")
     ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],
                     help="tile columns (default 200; smaller values are profiling cases, not bench lines)")
-    ap.add_argument("--workload", default="spatiotemporal", choices=["spatiotemporal", "batched", "serving"],
+    ap.add_argument("--workload", default="spatiotemporal", choices=["spatiotemporal", "batched", "serving", "selections"],
                     help="spatiotemporal: the n = 204,864 matrix (default); batched: 64 uneven matrices per "
-                         "launch; serving: request server under Poisson arrivals")
+                         "launch; serving: request server under Poisson arrivals; selections: Sigma "
+                         "only from tile column f on (f = 0, nt/2, nt)")
     ap.add_argument("--precision", default="emu64", choices=["fp64", "emu64", "fp32x"], help="serving precision")
     ap.add_argument("--serve-window", type=float, default=30.0, help="serving: seconds of arrivals per phase")
     ap.add_argument("--serve-gb", type=float, default=120.0, help="serving: data arena (GiB)")
@@ -710,6 +794,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "serving":
         run_serving(args, world, rank, local)
+    elif args.workload == "selections":
+        run_selections(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 
