@@ -284,6 +284,33 @@ struct Builder {
       for (int c0 = 0; c0 < L.nblk(k); c0 += step) terms.push_back({k, c0, std::min(L.nblk(k), c0 + step) - 1});
     }
     for (int c = 0; c < cq; ++c) terms.push_back({kq, c, c});  // same tile column: one block column per task
+    // A block of block column cq is due when the factorization frontier
+    // reaches that column. Its one-block-column terms from an earlier tile
+    // column whose source lies more than kFuseReach block columns before cq
+    // are final long before that: merge runs of them into one task of up to
+    // kFuseCols block columns (a longer inner length: the epilogue, completion
+    // and, in the emulated modes, the recombination are paid once per run
+    // instead of once per column). Terms from this tile column, which arrive
+    // one frontier step at a time, the nearer terms and the block's newest
+    // term stay single.
+    constexpr int64_t kFuseReach = 8;
+    constexpr int kFuseCols = 8;
+    {
+      std::vector<Term> merged;
+      for (size_t q = 0; q < terms.size(); ++q) {
+        const Term& t = terms[q];
+        if (!merged.empty() && q + 1 < terms.size()) {
+          Term& p = merged.back();
+          if (t.k < kq && p.k == t.k && t.c0 == t.c1 && p.c1 + 1 == t.c0 && t.c1 - p.c0 < kFuseCols &&
+              grow(kq, cq) - grow(t.k, t.c1) > kFuseReach) {
+            p.c1 = t.c1;
+            continue;
+          }
+        }
+        merged.push_back(t);
+      }
+      terms.swap(merged);
+    }
     const int64_t outref = mkref(BUF_L, L.blk(i, kq, r, cq));
     const int ld_i = L.rows(i);
     int nwritten = 0;
