@@ -887,6 +887,42 @@ __device__ __forceinline__ void trsm_rows_lt(double* X, const double* T, const d
   }
 }
 
+// X (m x n, m <= 16) <- X T^{-T} with the row values in registers: T lower
+// n x n with its strict lower part already divided by the pivot of its column
+// (Tn[c][j] = T[c][j] / T[j][j]), rcp[j*LDS] = 1 / T[j][j]. Warp w owns rows
+// 4w .. 4w+3; the 8 lanes of a row hold its columns ph, ph+8, ... (ph = lane /
+// 4). Step j takes the finished (not yet scaled) value y_j of each row from
+// the lane that holds it (a shuffle) and subtracts y_j Tn[c][j] from the
+// columns c > j; x = y / diag(T) at the end. No shared-memory round trip and
+// no one-lane scaling between two steps.
+__device__ __forceinline__ void trsm_rows_lt16(double* X, const double* Tn, const double* rcp, int m, int n) {
+  static_assert(FB == 64, "8 lanes x 8 columns per row");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = warp * 4 + (lane & 3), ph = lane >> 2;
+  const bool own = r < m;
+  double y[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = ph + 8 * q;
+    y[q] = own && c < n ? X[r * LDS + c] : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < FB; ++j) {
+    if (j >= n) break;
+    const double yj = __shfl_sync(0xffffffffu, y[j >> 3], (lane & 3) + 4 * (j & 7));
+#pragma unroll
+    for (int q = j >> 3; q < 8; ++q) {
+      const int c = ph + 8 * q;
+      if (c > j) y[q] = fma(-yj, Tn[c * LDS + j], y[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = ph + 8 * q;
+    if (own && c < n) X[r * LDS + c] = y[q] * rcp[c * LDS];
+  }
+}
+
 // X (m x n) <- T^{-1} X, T lower m x m, rcp[j*LDS] = 1 / T[j][j]. Columns are
 // independent; warp w owns columns 4q + w (interleaved, so that the
 // triangular work of an inverse is balanced). `lower` skips the columns c > j
@@ -1111,7 +1147,15 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
       double* rcp = T + FB;  // column FB of T's padded rows is free: rcp[j * LDS]
       if (tid < n) rcp[tid * LDS] = 1.0 / T[tid * LDS + tid];
       __syncthreads();
-      trsm_rows_lt(X, T, rcp, sb.rm, n);
+      if (sb.rm <= 16) {  // every part of a row-split block
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int c = warp + 1; c < n; c += NTHREADS / 32)
+          for (int j = lane; j < c; j += 32) T[c * LDS + j] *= rcp[j * LDS];
+        __syncthreads();
+        trsm_rows_lt16(X, T, rcp, sb.rm, n);
+      } else {
+        trsm_rows_lt(X, T, rcp, sb.rm, n);
+      }
       __syncthreads();
       store_sub(p, tk, sb, X, false);
       break;
