@@ -42,11 +42,11 @@ METRIC = "factor+selinv TFLOP/s (FP64)"
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
 # DRAM traffic of the persistent kernel per launch, from ncu captures of the
-# nt = 8 and nt = 16 cases of the same matrix family (0.826 GB and 2.230 GB):
+# nt = 8 and nt = 16 cases of the same matrix family (0.809 GB and 2.164 GB):
 # the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
-TRAFFIC = {"sources_sha": "8f2b5e00cdce1223", "bytes_per_launch": 34.51e9}
+TRAFFIC = {"sources_sha": "38f9aef84c77b0ad", "bytes_per_launch": 33.33e9}
 
 
 def kernel_sources_sha() -> str:

@@ -285,14 +285,13 @@ struct Builder {
     }
     for (int c = 0; c < cq; ++c) terms.push_back({kq, c, c});  // same tile column: one block column per task
     // A block of block column cq is due when the factorization frontier
-    // reaches that column. Its one-block-column terms from an earlier tile
-    // column whose source lies more than kFuseReach block columns before cq
-    // are final long before that: merge runs of them into one task of up to
-    // kFuseCols block columns (a longer inner length: the epilogue, completion
-    // and, in the emulated modes, the recombination are paid once per run
-    // instead of once per column). Terms from this tile column, which arrive
-    // one frontier step at a time, the nearer terms and the block's newest
-    // term stay single.
+    // reaches that column. Its one-block-column terms whose source lies more
+    // than kFuseReach block columns before cq are final long before that:
+    // merge runs of them (one source tile column per run) into one task of up
+    // to kFuseCols block columns (a longer inner length: the epilogue,
+    // completion and, in the emulated modes, the recombination are paid once
+    // per run instead of once per column). The nearer terms, which arrive one
+    // frontier step at a time, and the block's newest term stay single.
     constexpr int64_t kFuseReach = 8;
     constexpr int kFuseCols = 8;
     {
@@ -301,7 +300,7 @@ struct Builder {
         const Term& t = terms[q];
         if (!merged.empty() && q + 1 < terms.size()) {
           Term& p = merged.back();
-          if (t.k < kq && p.k == t.k && t.c0 == t.c1 && p.c1 + 1 == t.c0 && t.c1 - p.c0 < kFuseCols &&
+          if (p.k == t.k && t.c0 == t.c1 && p.c1 + 1 == t.c0 && t.c1 - p.c0 < kFuseCols &&
               grow(kq, cq) - grow(t.k, t.c1) > kFuseReach) {
             p.c1 = t.c1;
             continue;
