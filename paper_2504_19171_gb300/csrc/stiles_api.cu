@@ -84,7 +84,21 @@ struct stiles_handle {
   bool launched = false;
   int last_kind = -1;         // plan kind of the last launch
   int last_factor_kind = -1;  // plan kind of the last launch that factorized
+  bool mirror_ok = false;     // fused plan: every final Sigma write (NEG, SYMUPD) lands in the Sigma buffer
 };
+
+// The kernel mirrors the writes of the fused plan's NEG and SYMUPD tasks to a
+// host buffer at their offset in the Sigma buffer: allowed only when every
+// such write (output block, and the mirror block of an off-diagonal SYMUPD)
+// is in the Sigma buffer.
+static bool sigma_writes_in_sigma(const Plan& p) {
+  for (const Task& t : p.tasks) {
+    if (t.op != OP_NEG && t.op != OP_SYMUPD) continue;
+    if ((t.out >> BUF_SHIFT) != BUF_S) return false;
+    if (t.op == OP_SYMUPD && !(t.flags & TF_SYM_DIAG) && (t.aux >> BUF_SHIFT) != BUF_S) return false;
+  }
+  return true;
+}
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -167,6 +181,7 @@ static int create_handle(int nt, int b, int band, int arrow, int precision, int 
     free_handle(h);
     return rc;
   }
+  h->mirror_ok = sigma_writes_in_sigma(h->plans[PLAN_FUSED]);
   Layout L(h->s);
   h->w_bytes = align_up((size_t)L.doubles() * sizeof(double), 256);
   h->ctr_offset = h->w_bytes;
@@ -284,7 +299,8 @@ extern "C" int stiles_factor_selinv_host(stiles_t h, const double* A_host, doubl
   double* S_map = (double*)mapped_host(S_host, bytes);
   const char *a0 = (const char*)A_host, *s0 = (const char*)S_host;
   const bool apart = a0 + bytes <= s0 || s0 + bytes <= a0;
-  if (A_map && S_map && apart) return launch(h, PLAN_FUSED, A_map, L_dev, S_dev, scratch, stream, S_map);
+  if (A_map && S_map && apart && h->mirror_ok)
+    return launch(h, PLAN_FUSED, A_map, L_dev, S_dev, scratch, stream, S_map);
   if (cudaMemcpyAsync(A_dev, A_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return STILES_ERR_CUDA;
   const int rc = launch(h, PLAN_FUSED, A_dev, L_dev, S_dev, scratch, stream);
   if (rc != STILES_OK) return rc;

@@ -1087,7 +1087,9 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
     case OP_NEG: {
       double* O = resolve(p, tk.out) + sb.r0 + (int64_t)sb.c0 * tk.ldo;
       const double* C = tk.op == OP_UPD ? resolve(p, tk.cin) + sb.r0 + (int64_t)sb.c0 * tk.ldc : nullptr;
-      // an off-diagonal Sigma block is final when its NEG task writes it
+      // an off-diagonal Sigma block is final when its NEG task writes it (the
+      // planner emits NEG and SYMUPD tasks only with outputs, and SYMUPD
+      // mirror blocks, in the Sigma buffer, so the offsets below stay inside it)
       double* Om = tk.op == OP_NEG && p.smirror ? p.smirror + (O - p.buf[BUF_S]) : nullptr;
 #pragma unroll
       for (int i = 0; i < TM; ++i)
