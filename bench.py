@@ -46,7 +46,7 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
-TRAFFIC = {"sources_sha": "38f9aef84c77b0ad", "bytes_per_launch": 33.33e9}
+TRAFFIC = {"sources_sha": "7ccf1b214a31ed44", "bytes_per_launch": 33.33e9}
 
 
 def kernel_sources_sha() -> str:

@@ -292,8 +292,13 @@ struct Builder {
     // completion and, in the emulated modes, the recombination are paid once
     // per run instead of once per column). The nearer terms, which arrive one
     // frontier step at a time, and the block's newest term stay single.
+    // A run lumps the work of a block's chain, which lengthens the factor's
+    // critical path: it pays only when the whole selected inversion runs in
+    // the same launch and keeps the GPU busy meanwhile (a fused plan of every
+    // column), not in a factor-only or column-selected plan, whose time is
+    // the factor's critical path.
     constexpr int64_t kFuseReach = 8;
-    constexpr int kFuseCols = 8;
+    const int kFuseCols = kind == PLAN_FUSED && s.sel0 == 0 ? 8 : 1;
     {
       std::vector<Term> merged;
       for (size_t q = 0; q < terms.size(); ++q) {
