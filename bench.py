@@ -684,7 +684,9 @@ def run_selections(args, world, rank, local):
     requests whose earliest entry lies in tile column f (the plan keeps the
     whole factorization and phase 1 / phase 2 of the columns >= f only):
     f = 0 (every column), nt/2, and nt (the arrow block: the fixed effects'
-    covariance). Each selected run's tiles are compared with the full run's."""
+    covariance). Each selected run's tiles are compared with the full run's
+    (max |difference| / max |Sigma|: the full plan merges far update terms into
+    runs, a selected plan keeps them single, so the two agree to rounding)."""
     import numpy as np
     import torch
 
@@ -730,16 +732,21 @@ def run_selections(args, world, rank, local):
         if code != S.STILES_OK:
             raise SystemExit(f"selection f={f}: {S.strerror(code)} info={info}")
         t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+        diff = None
         if f == 0:
             full_S, full_t = st.S, t
-            same = None
-        else:  # every tile of the selected columns, bit for bit
+        else:  # every tile of the selected columns against the full run's
             lay = st.layout
-            same = all(torch.equal(st.S[o:o + lay.rows(i) * lay.rows(k)], full_S[o:o + lay.rows(i) * lay.rows(k)])
-                       for i, k in lay.pattern() if k >= f for o in [lay.offset(i, k)])
+            num = den = 0.0
+            for i, k in lay.pattern():
+                if k >= f:
+                    o, sz = lay.offset(i, k), lay.rows(i) * lay.rows(k)
+                    num = max(num, (st.S[o:o + sz] - full_S[o:o + sz]).abs().max().item())
+                    den = max(den, full_S[o:o + sz].abs().max().item())
+            diff = num / den
         rows.append({"first_column": f, "ms_per_step": 1e3 * t / args.steps, "flops_per_step": flops,
                      "tflops": whole_job_rate(world, args.steps, flops, t) / 1e12,
-                     "speedup_vs_full": full_t / t, "bitwise_equal_to_full": same})
+                     "speedup_vs_full": full_t / t, "max_rel_diff_vs_full": diff})
         if f != 0:
             st.S = None
         st.close()

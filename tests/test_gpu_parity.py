@@ -168,3 +168,26 @@ def test_fp32_class_error_is_reported(shape):
     err = rel_err(Sg, Sr)
     print(f"FP32-class {shape}: Sigma rel err {err:.3e}, L rel err {rel_err(L, Lr):.3e}, logdet abs err {abs(ld - ldr):.3e}")
     assert err < 1e-4
+
+
+MERGED_RUN_SHAPES = [(3, 640, 1, 16), (4, 576, 2, 9)]  # blocks far enough apart for update runs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", MERGED_RUN_SHAPES)
+def test_update_runs_parity(shape):
+    """Shapes whose fused plan merges far update terms into runs: the fused
+    FP64 and EMU64 results against the oracle, and against the factor +
+    selinv calls (single terms), which agree to rounding."""
+    M = W.random_arrowhead(*shape, seed=sum(shape) + 5)
+    _, Sr, ldr = O.selinv(M)
+    _, S_fused, ld_fused, st_fused = run_gpu(M, "fused")
+    _, S_split, ld_split, st_split = run_gpu(M, "split")
+    _, S_emu, ld_emu, st_emu = run_gpu(M, "fused", precision=1)
+    assert st_fused[0] == 0 and st_split[0] == 0 and st_emu[0] == 0
+    assert rel_err(S_fused, Sr) < FP64_TOL
+    assert rel_err(S_split, Sr) < FP64_TOL
+    assert rel_err(S_fused, S_split) < 1e-13
+    assert rel_err(S_emu, Sr) < 1e-12
+    for ld in (ld_fused, ld_split, ld_emu):
+        assert abs(ld - ldr) < 1e-10 * abs(ldr)

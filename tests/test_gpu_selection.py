@@ -1,7 +1,8 @@
 """General selections on the GPU: a selected plan's Sigma columns are
-bit-identical to the full selected inversion and earlier columns are not
-written; the full inverse (band widened to every tile) against the dense
-inverse."""
+bit-identical to the full selected inversion on shapes where both plans run
+the same update tasks (and agree to rounding where the full plan merges far
+update terms into runs), earlier columns are not written; the full inverse
+(band widened to every tile) against the dense inverse."""
 import numpy as np
 import pytest
 
@@ -51,3 +52,30 @@ def test_full_inverse_case6(shape):
     assert rel_err(Sg, ref) < FP64_TOL
     _, Sr, _ = O.selinv(F)
     assert rel_err(Sg, Sr) < FP64_TOL
+
+
+@pytest.mark.gpu
+def test_selected_columns_where_the_full_plan_merges_update_runs():
+    """(3, 640, 1, 16): the full fused plan merges far update terms into runs,
+    a selected plan keeps single terms; its columns agree with the full run's
+    to rounding and with the oracle."""
+    S = need_gpu()
+    import torch
+    shape, first = (3, 640, 1, 16), 1
+    M = W.random_arrowhead(*shape, seed=77)
+    _, S_full, _, _ = run_gpu(M, "fused")
+    _, Sr, ldr = O.selinv(M)
+    st = S.Stiles(*shape, wait_budget_s=5.0, first_column=first).upload(M)
+    try:
+        st.S.fill_(float("nan"))
+        st.factor_selinv()
+        torch.cuda.synchronize()
+        assert st.status()[0] == S.STILES_OK
+        assert abs(st.logdet() - ldr) < 1e-10 * abs(ldr)
+        Ssel = st.sigma_tiles()
+    finally:
+        st.close()
+    sel = {key: T for key, T in Ssel.items() if key[1] >= first}
+    assert rel_err(sel, {key: S_full[key] for key in sel}) < 1e-13
+    assert rel_err(sel, {key: Sr[key] for key in sel}) < FP64_TOL
+    assert all(np.all(np.isnan(T)) for key, T in Ssel.items() if key[1] < first)

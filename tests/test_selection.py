@@ -61,3 +61,24 @@ def test_first_column_for_entries():
     assert S.first_column_for([(79, 3), (40, 41)], nt, b) == 0
     assert S.first_column_for([(47, 41), (60, 80)], nt, b) == 5
     assert S.first_column_for([(85, 83)], nt, b) == nt  # arrow x arrow: the corner column only
+
+
+def test_update_runs_only_in_full_fused_plans():
+    """The planner merges far one-block-column update terms into runs only in
+    a fused plan of every column: that plan has fewer tasks than the factor
+    and selected-inversion plans together, while a column-selected fused plan
+    has exactly their sum (single terms). Every one of these plans validates
+    (satisfiable waits, in-bounds accesses)."""
+    from paper_2504_19171_gb300 import stiles as S
+    for shape in [(3, 640, 1, 16), (4, 576, 2, 9), (2, 1024, 1, 8)]:
+        fac = S.stiles_plan_stats(*shape, S.PLAN_FACTOR)["tasks"]
+        fused = S.stiles_plan_stats(*shape, S.PLAN_FUSED)["tasks"]
+        sel = S.stiles_plan_stats(*shape, S.PLAN_SELINV)["tasks"]
+        assert fused < fac + sel, shape
+        assert S.stiles_debug_validate(*shape, S.PLAN_FUSED) == S.STILES_OK, shape
+        for first in (1, shape[0]):
+            which = first << 16
+            f = S.stiles_plan_stats(*shape, S.PLAN_FUSED + which)["tasks"]
+            s = S.stiles_plan_stats(*shape, S.PLAN_SELINV + which)["tasks"]
+            assert f == fac + s, (shape, first)
+            assert S.stiles_debug_validate(*shape, S.PLAN_FUSED + which) == S.STILES_OK, (shape, first)
