@@ -130,7 +130,12 @@ int stiles_create_tuned(int nt, int b, int band, int arrow, int precision, int t
  * This handle computes Sigma on L's pattern for tile columns >= first_column
  * and writes no Sigma tile of earlier columns. 0 <= first_column <= nt (< nt
  * without an arrow). The full inverse (Fig. 2 case 6) is the pattern with
- * band = nt - 1: pack the tiles outside A's own band as zeros. */
+ * band = nt - 1: pack the tiles outside A's own band as zeros.
+ * Task cutting: the fused plan of every column (first_column 0) applies the
+ * factor's far update terms in runs of several block columns, for
+ * throughput; the factor-only plan and the fused plans with first_column > 0
+ * apply them one block column at a time, for the shortest critical path. The
+ * two cuttings give L, logdet and Sigma that agree up to rounding. */
 int stiles_create_selected(int nt, int b, int band, int arrow, int precision, int first_column, stiles_t *out);
 
 /* Doubles of one packed A / L / Sigma buffer (see the layout above). */
