@@ -282,7 +282,7 @@ int stiles_debug_validate(int nt, int b, int band, int arrow, int which);
 /* Test hook: build the plan `which` for a shape, corrupt its dependency table
  * on the host (mode 1: one wait names a counter beyond the table; mode 2: one
  * wait needs one more signal than exists; mode 3: a wait on a task later in
- * claim order) and return the consistency check's verdict (expected
+ * claim order) and return the consistency check's result (expected
  * STILES_ERR_PLAN). Host only. */
 int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode);
 
