@@ -20,7 +20,10 @@
 // from a stale L1 line) and accumulates up to a 64 x 64 block in registers
 // (4 x 8 per thread). The reduced-precision modes replace the products of
 // the bulk tasks: emulated FP64 (bf16 digit products on the tensor cores)
-// and FP32-class (FP32 FMA).
+// and FP32-class (FP32 FMA). In the end-to-end call the matrix may live in
+// page-locked host memory (read over the host link by the tasks that first
+// load each block) and every final Sigma write is repeated into a host
+// buffer, so the transfers overlap the computation.
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
