@@ -185,6 +185,32 @@ def oracle_sample(nt_sample: int):
     return time.perf_counter() - t0, flops
 
 
+def oracle_sample_all_cores(nt_sample: int):
+    """The same single-thread oracle sample run as independent copies, one
+    process per host core, all at once (independent problems: the oracle is
+    not changed); returns (aggregate TFLOP/s over the overlapped run, cores),
+    or (None, reason)."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    code = ("import json, sys, time; sys.path.insert(0, sys.argv[1]); import bench; "
+            "dt, f = bench.oracle_sample(int(sys.argv[2])); t1 = time.time(); "
+            "print(json.dumps({'start': t1 - dt, 'end': t1, 'flops': f}))")
+    procs = [subprocess.Popen([sys.executable, "-c", code, ROOT, str(nt_sample)], stdout=subprocess.PIPE,
+                              stderr=subprocess.DEVNULL, text=True) for _ in range(cores)]
+    runs = []
+    for p in procs:
+        out, _ = p.communicate()
+        try:
+            runs.append(json.loads(out.strip().splitlines()[-1]))
+        except (ValueError, IndexError):
+            runs = None
+        if p.returncode != 0 or runs is None:
+            for q in procs:
+                q.wait()
+            return None, f"a copy failed (exit {p.returncode})"
+    wall = max(r["end"] for r in runs) - min(r["start"] for r in runs)
+    return sum(r["flops"] for r in runs) / wall / 1e12, cores
+
+
 def run_reference(args, world, rank):
     """CPU oracle arm: rank 0 only; each step = the oracle on the bounded sample."""
     if rank != 0:
@@ -672,6 +698,12 @@ def run_ours(args, world, rank, local):
                                 "sample": f"first {SAMPLE_NT} tile columns + arrow of the same matrix family "
                                           f"(n = {SAMPLE_NT * 1024 + 64}, {f / 1e9:.2f} GFLOP) in {dt:.1f} s",
                                 "host": host_info(), "n1040_seconds_best_of_3": oracle_n1040_seconds()}
+        v_all, cores = oracle_sample_all_cores(SAMPLE_NT)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": v_all, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": "one copy of the same single-thread sample per host core, all at once (independent "
+                      "problems); flops of all copies / wall time from the first start to the last end"
+            if v_all is not None else f"not measured: {cores}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
