@@ -53,3 +53,18 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(A(), 2, 1)  # rank 1: no work, no output
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_throughput_on_all_host_cores():
+    """The bench's all-cores CPU baseline: one copy of the single-thread oracle
+    sample per host core, run as separate processes; the aggregate is every
+    copy's flops over the overlapped wall time (positive, and not above cores
+    x a single copy's rate beyond timing noise)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    value, cores = bench.oracle_sample_all_cores(1)
+    assert isinstance(cores, int) and cores >= 1
+    assert value is not None and value > 0
+    dt, flops = bench.oracle_sample(1)
+    single = flops / dt / 1e12
+    assert value <= cores * single * 1.5
