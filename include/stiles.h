@@ -186,7 +186,8 @@ int stiles_factor_selinv(stiles_t h, const double *A_tiles, double *L_tiles, dou
  *   - otherwise: copy A_host into A_dev, run the fused call, copy Sigma_dev
  *     back into Sigma_host (page-locked buffers make the copies asynchronous;
  *     A_host and Sigma_host may then be the same buffer).
- * Host buffers must stay valid until the stream reaches the end of the call.
+ * Host buffers must stay valid, A_host unchanged and Sigma_host unread, until
+ * the stream reaches the end of the call.
  * Device buffers follow the rules of stiles_factor_selinv (A_dev may alias
  * L_dev; Sigma_dev holds the full result in both ways). Asynchronous: read
  * the status / logdet afterwards as usual. */
