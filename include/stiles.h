@@ -108,16 +108,20 @@ enum stiles_precision { STILES_FP64 = 0, STILES_EMU64 = 1, STILES_FP32X = 2 };
 int stiles_create(int nt, int b, int band, int arrow, int precision, stiles_t *out);
 
 /* Same as stiles_create with a tuning code (0 = the defaults; the project's
- * autotuner picks one per (b, band, arrow blocks, precision)). It changes
- * only how the work is cut into tasks. Bits 2-5 split output blocks among
- * CTAs differently (bit-identical results); bits 0-1 group the factor's
- * update terms differently (results equal up to rounding):
+ * autotuner picks one per (b, band, arrow blocks, precision)). Bits 0-5
+ * change only how the work is cut into tasks: bits 2-5 split output blocks
+ * among CTAs differently (bit-identical results); bits 0-1 group the
+ * factor's update terms differently (results equal up to rounding). Bit 6
+ * changes which products a reduced-precision handle lowers:
  *   bits 0-1  factor: source block columns per update task for tile columns
  *             older than k-1 (0: 8, 1: 4, 2: 16, 3: 32)
  *   bits 2-3  phase 2: parts of an off-diagonal Sigma block task
  *             (0: four 32 x 32 quadrants, 1: two 32-row halves, 2: whole)
  *   bits 4-5  factor: parts of the newest update of an off-diagonal block
  *             (0: four quadrants, 1: whole)
+ *   bit 6     STILES_EMU64 / STILES_FP32X: also lower the block updates inside
+ *             each diagonal tile (its POTRF's own SYRK / GEMM steps); with 0
+ *             the whole diagonal-tile POTRF runs in true FP64
  * Other codes return STILES_ERR_INVALID_ARG. */
 int stiles_create_tuned(int nt, int b, int band, int arrow, int precision, int tuning, stiles_t *out);
 
@@ -210,6 +214,11 @@ int stiles_factor_selinv_host(stiles_t h, const double *A_host, double *Sigma_ho
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture begins.
+ *   - The looked-up address stays valid while the library's device code
+ *     stays loaded in that device's context. A device reset (cudaDeviceReset,
+ *     or a reset of the primary context by another library) unloads it: the
+ *     cached address is then stale, so do not call this entry point on that
+ *     device again in the same process after such a reset.
  *   - Every call, from every handle, shares the one array and leaves its
  *     contents behind; each call re-initialises the part that must start from
  *     a known state (the scheduler state) on its stream before the launch.
@@ -268,10 +277,12 @@ int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size
  *     GEMM 2 m n k),
  * [5] phase-2 tile GEMMs: (tile, tile) products accumulated into Sigma tiles
  *     (the count of the GEMM-count table of Sec. III-E and Appendix A),
- * [6] critical path and [7] list-schedule makespan, in estimated ns.
+ * [6] critical path and [7] list-schedule makespan, in estimated ns,
+ * [8] the part of [4] that runs as block products in the plan's reduced
+ *     precision (0 for STILES_FP64; the rest stays on the FP64 pipe).
  * Returns STILES_ERR_INVALID_ARG for a bad shape, STILES_ERR_PLAN if the
  * table fails its consistency check. */
-int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]);
+int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[9]);
 
 /* Test hook: build the plan `which` (as in stiles_plan_stats) for a shape and
  * emulate one launch of it on the host: every memory access of every task
@@ -354,7 +365,7 @@ int stiles_batch_logdet(stiles_batch_t h, double *out_host);
 int stiles_batch_set_option(stiles_batch_t h, int option, long long value);
 
 /* Plan statistics of the merged table (same fields as stiles_plan_stats). */
-int stiles_batch_stats(stiles_batch_t h, long long stats[8]);
+int stiles_batch_stats(stiles_batch_t h, long long stats[9]);
 
 /* --------------------------------------------------------------- server --
  * Request server with continuous batching (no counterpart in the paper; its

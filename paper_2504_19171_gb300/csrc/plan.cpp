@@ -59,6 +59,8 @@ struct Builder {
   std::vector<char> chain;                    // 1: writers strictly ordered
   std::vector<std::vector<int32_t>> writers;  // emission ids in signal order
   double flops = 0;
+  double flops_lowered = 0;  // algorithmic flops of the reduced-precision block products
+  bool sym_block = false;    // the next emitted task updates a symmetric diagonal block (m^2 k per term)
   long long tile_gemms = 0;
   int ndiag = 0;
 
@@ -76,6 +78,10 @@ struct Builder {
   int emit(Task t, std::vector<Seg> segs, std::vector<Wait> waits, std::vector<int32_t> sigs, double epi_ns) {
     double f = 0;
     for (const Seg& g : segs) f += 2.0 * t.m * t.n * g.k;
+    // the same products under the counting convention (a symmetric diagonal
+    // block's update counts m^2 k, like SYRK), for the reduced-precision share
+    if (t.prec != PREC_FP64) flops_lowered += sym_block ? 0.5 * f : f;
+    sym_block = false;
     if (t.pmode == PM_TRI3) f *= 0.75;
     if (t.prec == PREC_EMU64) f /= 10.0;   // measured order of the emulated-FP64 speed-up per block
     if (t.prec == PREC_FP32X) f /= 25.0;
@@ -343,11 +349,14 @@ struct Builder {
       if (diag) split(tk, PM_TRI3);
       else if (t + 1 == nchain && tune_upd_split(s.tune) == 0) split(tk, PM_QUAD4);
       if (grow(i, r) - grow(terms[t].k, terms[t].c1) <= kUrgentReach) tk.flags |= TF_URGENT;
-      lower_precision(tk);
+      // the diagonal tile's own updates belong to its POTRF, which stays true
+      // FP64 unless the tuning code lowers them too
+      if (!(i == kq && terms[t].k == kq) || tune_lower_diag(s.tune)) lower_precision(tk);
       std::vector<Wait> w;
       if (nwritten > 0) w.push_back({me, nwritten});
       if (nwritten == 0 && serve) w.push_back({prep_ctr[kq], 1});
       term_waits(terms[t], w);
+      sym_block = diag;
       emit(tk, {term_seg(terms[t])}, w, {me}, 0.0);
       ++nwritten;
     }
@@ -575,6 +584,7 @@ struct Builder {
           w.push_back({ucol(k, i, c), L.nblk(k)});
         }
         if (!segs.empty()) lower_precision(t);  // the products; the assembly (cin - acc, mirror) stays FP64
+        sym_block = r == c;
         emit(t, segs, w, {srow(i, i, r), scol(i, i, c)}, 0.0);
       }
     tile_gemms += (long long)st.size();
@@ -703,6 +713,7 @@ struct Builder {
     p.nctr = (int32_t)chain.size();
     p.ndiag = ndiag;
     p.flops = flops;
+    p.flops_lowered = flops_lowered;
     p.tile_gemms = tile_gemms;
     p.cp_ns = cp;
     p.makespan_ns = now;
@@ -827,6 +838,7 @@ int build_batch_plan(const std::vector<Shape>& shapes, const std::vector<int64_t
     M.ndiag += B.ndiag;
     M.tile_gemms += B.tile_gemms;
     M.flops += tile_flops(shapes[m], PLAN_FUSED);
+    M.flops_lowered += B.flops_lowered;
     (*diag_base)[m + 1] = M.ndiag;
   }
   const int rc = M.finish(workers);

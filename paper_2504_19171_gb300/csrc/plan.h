@@ -118,10 +118,15 @@ enum PlanKind : int { PLAN_FACTOR = 0, PLAN_SELINV = 1, PLAN_FUSED = 2 };
 //             (0: four 32 x 32 quadrants, 1: two 32-row halves, 2: whole block)
 //   bits 4-5  factor: parts of the newest update of an off-diagonal block
 //             (0: four quadrants, 1: whole block)
-enum : int { kTuneBits = 6 };
+//   bit 6     reduced-precision plans: the block updates inside a diagonal
+//             tile (the SYRK / GEMM steps of that tile's POTRF) also run in
+//             the reduced precision (0: they stay FP64, so that the whole
+//             diagonal-tile POTRF is true FP64). This one changes rounding.
+enum : int { kTuneBits = 7 };
 inline int tune_chunk_old(int t) { const int v[4] = {8, 4, 16, 32}; return v[t & 3]; }
 inline int tune_p2_split(int t) { return (t >> 2) & 3; }
 inline int tune_upd_split(int t) { return (t >> 4) & 3; }
+inline bool tune_lower_diag(int t) { return (t >> 6) & 1; }
 inline bool tune_valid(int t) { return t >= 0 && t < (1 << kTuneBits) && tune_p2_split(t) <= 2 && tune_upd_split(t) <= 1; }
 
 struct Shape {
@@ -157,6 +162,7 @@ struct Plan {
   int32_t nctr = 0;         // dependency counters used
   int32_t ndiag = 0;        // logdet partial sums (one per POTRF task)
   double flops = 0;         // algorithmic flops (tile-operation convention)
+  double flops_lowered = 0; // the part of them run as block products in the plan's reduced precision
   long long tile_gemms = 0; // phase-2 (tile, tile) products
   double cp_ns = 0;         // critical path of the estimated task graph
   double makespan_ns = 0;   // list-schedule makespan on `workers` workers

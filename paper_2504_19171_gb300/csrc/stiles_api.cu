@@ -425,7 +425,7 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
   }
 }
 
-extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[8]) {
+extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[9]) {
   const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
   if (!stats || kind < 0 || kind > 2 || prec > PREC_FP32X || workers < 1 || !tune_valid(tune))
     return STILES_ERR_INVALID_ARG;
@@ -442,6 +442,7 @@ extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, 
   stats[5] = p.tile_gemms;
   stats[6] = (long long)p.cp_ns;
   stats[7] = (long long)p.makespan_ns;
+  stats[8] = (long long)p.flops_lowered;
   return STILES_OK;
 }
 
@@ -862,7 +863,7 @@ extern "C" int stiles_batch_set_option(stiles_batch_t h, int option, long long v
   }
 }
 
-extern "C" int stiles_batch_stats(stiles_batch_t h, long long stats[8]) {
+extern "C" int stiles_batch_stats(stiles_batch_t h, long long stats[9]) {
   if (!h || !stats) return STILES_ERR_INVALID_ARG;
   stats[0] = h->dev.ntasks;
   stats[1] = 0;
@@ -872,6 +873,7 @@ extern "C" int stiles_batch_stats(stiles_batch_t h, long long stats[8]) {
   stats[5] = h->plan.tile_gemms;
   stats[6] = (long long)h->plan.cp_ns;
   stats[7] = (long long)h->plan.makespan_ns;
+  stats[8] = (long long)h->plan.flops_lowered;
   return STILES_OK;
 }
 

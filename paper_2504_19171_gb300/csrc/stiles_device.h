@@ -130,7 +130,7 @@ struct KParams {
 
 size_t kernel_smem_bytes();
 int kernel_threads();
-// Sets the kernel's dynamic shared-memory limit (once per process).
+// Sets the kernel's dynamic shared-memory limit on the current device (once per device).
 cudaError_t configure_persistent();
 const void* persistent_kernel_ptr();
 cudaError_t launch_persistent(const KParams& p, int grid, cudaStream_t stream);

@@ -27,7 +27,9 @@
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #include "plan.h"
 #include "stiles_device.h"
@@ -86,13 +88,16 @@ __device__ void raise_timeout(const KParams& p, long long where) {
   atomicExch(&p.st->abort, 1);
 }
 
-#ifdef STILES_CHECKED
-// Self-checking build: record the first violation (what, task, part) and stop.
+// Record the first violation of a table or queue invariant (what, task,
+// part) and stop every worker (STILES_DEV_CHECK, reported as a plan error).
 __device__ void check_fail(const KParams& p, int what, long long t, int q) {
   if (atomicCAS(&p.st->code, 0, STILES_DEV_CHECK) == 0)
     p.st->info = ((unsigned long long)(t & 0xffffffffll) << 16) | ((unsigned long long)q << 8) | (unsigned)what;
   atomicExch(&p.st->abort, 1);
 }
+
+#ifdef STILES_CHECKED
+// Self-checking build: every invariant below is checked.
 #define STILES_CHECK(cond, what, t, q) \
   do {                                  \
     if (!(cond)) check_fail(p, what, t, q); \
@@ -115,17 +120,29 @@ __device__ __forceinline__ void push_task(const KParams& p, int t) {
   }
   const Task tk = load_task(p, t);
   const int parts = tk.parts;
+  // The queue capacities are checked in every build (one compare on an
+  // atomic path): a table that would overflow a queue stops the launch with
+  // a check failure instead of writing past the slots.
   if (tk.flags & TF_URGENT) {
     const int pos = atomicAdd(p.q.lo + 8, parts);
-    STILES_CHECK(pos + parts <= p.ucap, 1, t, 0);
+    if (pos + parts > p.ucap) {
+      check_fail(p, 1, t, 0);
+      return;
+    }
     for (int q = 0; q < parts; ++q) store_release_i(p.q.uslots + pos + q, 4 * t + q);
     atomicAdd(p.q.lo + 24, parts);
     return;
   }
   const int b = t / kTasksPerBucket;
-  STILES_CHECK(b < p.nbuckets && t >= 0, 2, t, 0);
+  if (b >= p.nbuckets || t < 0) {
+    check_fail(p, 2, t, 0);
+    return;
+  }
   const int pos = atomicAdd(p.q.tail + b, parts);
-  STILES_CHECK(pos + parts <= p.bcap[b], 3, t, 0);
+  if (pos + parts > p.bcap[b]) {
+    check_fail(p, 3, t, 0);
+    return;
+  }
   for (int q = 0; q < parts; ++q) store_release_i(p.q.slots + (size_t)b * kSlotsPerBucket + pos + q, 4 * t + q);
   atomicAdd(p.q.avail + b, parts);
   atomicAdd(p.q.gcnt + (b >> 5), parts);
@@ -264,7 +281,10 @@ __device__ int pop_urgent_lane0(const KParams& p, unsigned long long start) {
   if (p.ucap <= 0) return -3;
   const int uh = claim(p.q.lo + 24, p.q.lo + 16);
   if (uh < 0) return -3;
-  STILES_CHECK(uh < p.ucap, 4, uh, 0);
+  if (uh >= p.ucap) {  // claimed past the urgent queue (checked in every build)
+    check_fail(p, 4, uh, 0);
+    return -1;
+  }
   return wait_slot(p, p.q.uslots + uh, start);
 }
 
@@ -313,8 +333,12 @@ __device__ int pop_task(const KParams& p, unsigned long long deadline) {
               if (h >= 0) {
                 atomicSub(p.q.gcnt + gi, 1);
                 atomicSub(p.q.scnt + (gi >> 5), 1);
-                STILES_CHECK(h < p.bcap[bb], 5, bb, 0);
-                got = wait_slot(p, p.q.slots + (size_t)bb * kSlotsPerBucket + h, start);
+                if (h >= p.bcap[bb]) {  // claimed past the bucket (checked in every build)
+                  check_fail(p, 5, bb, 0);
+                  got = -1;
+                } else {
+                  got = wait_slot(p, p.q.slots + (size_t)bb * kSlotsPerBucket + h, start);
+                }
               }
             }
             got = __shfl_sync(FULL, got, 0);
@@ -785,7 +809,10 @@ __device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, 
           const int k2 = rexp[row] + cexp[col] - kEmuScale + 8 * (EMU_S - 1);
           // 2^k2 built from its exponent bits when it is a normal double
           const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
-          res[j][q] = fma(v, sc, res[j][q]);
+          // a row or column holding an Inf or NaN (biased exponent 0x7ff, the
+          // largest there is) has no digits: its products are NaN, as in FP64
+          res[j][q] = (rexp[row] == 0x7ff || cexp[col] == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                                : fma(v, sc, res[j][q]);
         }
     }
     __syncthreads();
@@ -1354,12 +1381,23 @@ int kernel_threads() { return NTHREADS; }
 
 const void* persistent_kernel_ptr() { return (const void*)persistent_kernel; }
 
+// The shared-memory limit is a per-device attribute of the kernel: it is set
+// once for every device the process launches on (the current one here).
 cudaError_t configure_persistent() {
-  static bool configured = false;
-  if (configured) return cudaSuccess;
-  cudaError_t e =
-      cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kernel_smem_bytes());
-  if (e == cudaSuccess) configured = true;
+  constexpr int kMaxDevices = 64;
+  static std::atomic<bool> configured[kMaxDevices];
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices)
+    return cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kernel_smem_bytes());
+  if (configured[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  if (configured[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kernel_smem_bytes());
+  if (e == cudaSuccess) configured[dev].store(true, std::memory_order_release);
   return e;
 }
 

@@ -210,9 +210,10 @@ def stiles_set_option(h: int, option: int, value: int) -> None:
 
 def stiles_plan_stats(nt: int, b: int, band: int, arrow: int, which: int, workers: int = 152,
                       precision: int = STILES_FP64) -> Dict[str, int]:
-    st = (ctypes.c_longlong * 8)()
+    st = (ctypes.c_longlong * 9)()
     _check(_lib.stiles_plan_stats(nt, b, band, arrow, which + 16 * precision, workers, st), "stiles_plan_stats")
-    keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns"]
+    keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns",
+            "flops_lowered"]
     return dict(zip(keys, list(st)))
 
 
@@ -294,9 +295,10 @@ def stiles_batch_set_option(h: int, option: int, value: int) -> None:
 
 
 def stiles_batch_stats(h: int) -> Dict[str, int]:
-    st = (ctypes.c_longlong * 8)()
+    st = (ctypes.c_longlong * 9)()
     _check(_lib.stiles_batch_stats(h, st), "stiles_batch_stats")
-    keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns"]
+    keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns",
+            "flops_lowered"]
     return dict(zip(keys, st[:]))
 
 

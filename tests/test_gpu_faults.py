@@ -80,3 +80,22 @@ def test_bad_arguments_are_rejected():
     with pytest.raises(S.StilesError) as e:
         S.stiles_create(3, 8, 1, 2, precision=7)
     assert e.value.code == S.STILES_ERR_UNSUPPORTED
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("value", [np.nan, np.inf])
+@pytest.mark.parametrize("where", ["band", "arrow"])
+def test_nonfinite_off_diagonal_entry_is_reported(prec, value, where):
+    """A NaN or Inf in an off-diagonal tile of A (made on the host) reaches a
+    pivot through the factor's products in every precision mode: the launch
+    reports NOT_SPD instead of a finite, wrong Sigma. The emulated-FP64 digit
+    split turns a non-finite operand row or column into NaN products."""
+    S = need_gpu()
+    M = W.random_arrowhead(6, 100, 1, 9, seed=7)
+    if where == "band":
+        M.tiles[(1, 0)][17, 40] = value  # row 17 of L_10: reaches the pivots of tile 1 through SYRK
+    else:
+        M.tiles[(M.nt, 0)][3, 70] = value  # row 3 of the arrow: reaches the corner's pivots
+    _, _, _, status = run_gpu(M, "fused", precision=prec)
+    assert status[0] == S.STILES_ERR_NOT_SPD, (prec, where, status)

@@ -68,3 +68,20 @@ def test_oracle_throughput_on_all_host_cores():
     dt, flops = bench.oracle_sample(1)
     single = flops / dt / 1e12
     assert value <= cores * single * 1.5
+
+
+def test_reference_arm_loads_nothing_of_the_cuda_library():
+    """The CPU-oracle arm counts its flops with the closed form: in a fresh
+    interpreter, a sample run imports no module of the CUDA package but the
+    input generators and maps no library of it."""
+    import json
+    import subprocess
+    code = ("import json, sys; sys.path.insert(0, sys.argv[1]); import bench; bench.oracle_sample(1); "
+            "maps = open('/proc/self/maps').read(); "
+            "print(json.dumps({'mods': sorted(m for m in sys.modules if m.startswith('paper_2504_19171_gb300')), "
+            "'libstiles': 'libstiles' in maps}))")
+    out = subprocess.run([sys.executable, "-c", code, ROOT], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["mods"] == ["paper_2504_19171_gb300", "paper_2504_19171_gb300.workloads"]
+    assert r["libstiles"] is False

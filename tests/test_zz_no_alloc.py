@@ -1,7 +1,8 @@
 """The allocation-free entry point (stiles_factor_selinv_noalloc) gives the
 same L, Sigma and logdet as stiles_factor_selinv with a caller-allocated
-scratch, on two calls in a row (its fixed scratch array keeps the previous
-call's contents), and refuses shapes whose scratch does not fit the array.
+scratch and as the CPU oracle, on two calls in a row (its fixed scratch array
+keeps the previous call's contents), and refuses shapes whose scratch does
+not fit the array.
 
 Callers that cannot allocate device memory at call time (a service whose
 device memory is reserved once at start-up, code that must not call
@@ -9,6 +10,7 @@ cudaMalloc where it runs) use it. This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2504_19171_gb300 import workloads as W
 from tests.gpu_helpers import FP64_TOL, need_gpu, rel_err
 
@@ -18,6 +20,7 @@ def test_noalloc_matches_allocating_entry_point_twice():
     S = need_gpu()
     import torch
     M = W.random_arrowhead(16, 64, 1, 16, seed=5)
+    L_or, S_or, ld_or = O.selinv(M)
     st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=5.0).upload(M)
     try:
         assert S.stiles_workspace_bytes(st.h)[2] <= S.NOALLOC_SCRATCH_BYTES
@@ -39,6 +42,10 @@ def test_noalloc_matches_allocating_entry_point_twice():
             assert rel_err(Lg, L_ref) < FP64_TOL, call
             assert rel_err(Sg, S_ref) < FP64_TOL, call
             assert abs(ld - ld_ref) < FP64_TOL * abs(ld_ref), call
+            # and against the oracle directly (the same bar as every FP64 parity test)
+            assert rel_err(Lg, L_or) < FP64_TOL, call
+            assert rel_err(Sg, S_or) < FP64_TOL, call
+            assert abs(ld - ld_or) < FP64_TOL * abs(ld_or), call
     finally:
         st.close()
 
