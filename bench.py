@@ -40,6 +40,14 @@ METRIC = "factor+selinv TFLOP/s (FP64)"
 # FP64 FMA pipe of GB300: 2 DFMA per clock per SM (measured: 1.97/clk/SM with
 # >= 4 warps per SM), 152 SMs, 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+# SIMT FP32 FMA: 128 lanes per SM per clock.
+FP32_SIMT_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
+# Low-precision products per FP64-equivalent multiply-add of each reduced mode
+# (the digit-pair products of the split-precision scheme: with s digits per
+# operand the levels t + u <= s - 1 are kept, s (s + 1) / 2 products), and the
+# pipe that runs them.
+VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (mma.sync)", "digits": 7, "products": 28},
+                    "fp32x": {"pipe": "FP32 SIMT FMA", "digits": None, "products": 1}}
 
 # DRAM traffic of the persistent kernel per launch, from ncu captures of the
 # nt = 8 and nt = 16 cases of the same matrix family (0.809 GB and 2.164 GB):
@@ -47,6 +55,66 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
 TRAFFIC = {"sources_sha": "7ccf1b214a31ed44", "bytes_per_launch": 33.33e9}
+
+
+def measured_peaks() -> dict:
+    """Roofline denominators measured on the GB300s (driver-written
+    file: a cuBLAS bf16 GEMM as a burst and sustained, a copy for HBM), else
+    the fallback figures of an earlier GB300 measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def variant_roofline(name: str, flops: float, lowered: float, seconds: float, peaks: dict) -> dict:
+    """Roofline of a reduced-precision launch: the lowered block products run
+    on their pipe at (pipe peak / products per FP64-equivalent multiply-add),
+    the rest (block POTRF / TRSM sweeps, TRTRI, LAUUM, the diagonal tiles'
+    own updates) on the FP64 pipe; the two bounds add (Amdahl), giving the
+    fastest time the launch could take and, from it, the peak in
+    FP64-equivalent TFLOP/s."""
+    v = VARIANT_PRODUCTS[name]
+    if v["pipe"].startswith("bf16"):
+        pipe_peak, pipe_src = peaks["bf16_tflops"], f"bf16 tensor {peaks['bf16_tflops']:.1f} TFLOP/s ({peaks['source']}, burst)"
+    else:
+        pipe_peak, pipe_src = FP32_SIMT_PEAK_TFLOPS, f"FP32 SIMT {FP32_SIMT_PEAK_TFLOPS:.1f} TFLOP/s (nominal)"
+    t_low = lowered * v["products"] / (pipe_peak * 1e12)
+    t_64 = (flops - lowered) / (FP64_PEAK_TFLOPS * 1e12)
+    peak = flops / (t_low + t_64) / 1e12
+    achieved = flops / seconds / 1e12
+    return {"bound": "tensor+fp64" if v["pipe"].startswith("bf16") else "fp32+fp64", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s (FP64-equivalent)", "frac": achieved / peak, "traffic": None,
+            "lowered_flops": lowered, "fp64_flops": flops - lowered, "products_per_fma": v["products"],
+            "t_min_ms": {"lowered": 1e3 * t_low, "fp64": 1e3 * t_64},
+            "peak_derivation": f"lowered flops x {v['products']} products on {pipe_src}, plus the FP64 share on "
+                               f"the FP64 pipe ({FP64_PEAK_TFLOPS:.4f} TFLOP/s, derived); the times add"}
+
+
+def measure_fp64_gemm(dev, n: int = 8192, reps: int = 3) -> dict:
+    """cuBLAS DGEMM (torch.matmul, float64, n^3) on the device: the library's
+    FP64 rate, a measured reference beside the derived FP64-pipe peak."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    c = torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return {"tflops": 2.0 * n ** 3 / best / 1e12, "n": n, "seconds_best": best, "reps": reps,
+            "how": f"torch.matmul float64 {n}^3 (cuBLAS), best of {reps} after one warm-up, CUDA events"}
 
 
 def kernel_sources_sha() -> str:
@@ -269,10 +337,13 @@ def measure_variants(S, st, stream, dev, flops, logdet64, args):
         t = ev[0].elapsed_time(ev[-1]) / 1e3 / args.variant_steps
         ld = sv.logdet()
         err = float((sv.S - S64).abs().max().item()) / smax
+        lowered = S.stiles_plan_stats(st.nt, st.b, st.w, st.a, S.PLAN_FUSED + (tune << 8), 152,
+                                      precision=prec)["flops_lowered"]
         out[name] = {"value": flops / t / 1e12, "unit": "TFLOP/s (FP64-equivalent flops)", "ms_per_step": 1e3 * t,
                      "tuning": tune,
                      "steps": args.variant_steps, "speedup_vs_fp64": None,
-                     "sigma_err_vs_fp64": err, "logdet_rel_err_vs_fp64": abs(ld - logdet64) / abs(logdet64)}
+                     "sigma_err_vs_fp64": err, "logdet_rel_err_vs_fp64": abs(ld - logdet64) / abs(logdet64),
+                     "roofline": variant_roofline(name, flops, lowered, t, args.peaks)}
         sv.A = None
         sv.close()
         del sv
@@ -447,6 +518,68 @@ SERVE = {"workload": "served_sweep_requests", "pool": "64 shapes of the batched 
                    "band x rho, arrow as is, diagonal tau + rho rb + ra"}
 
 
+def serve_phase(S, srv, flops, arrivals, reqs, window, closed_conc=0):
+    """One serving window: starts the server kernel, feeds it and stops it.
+    ``arrivals`` are request times in seconds (open loop, queueing delay
+    included) or None for a closed loop that keeps ``closed_conc`` requests
+    in flight; ``reqs`` are (shape, tau, rho) triples drawn in advance.
+    Returns latency and throughput statistics."""
+    import numpy as np
+    srv.start(window + 120.0)
+    queue, start_t, lat, done_flops, done_n, failed = [], {}, [], 0.0, 0, 0
+    admitted, offered_n, not_admitted = 0, 0, 0
+    t_start = time.perf_counter()
+    in_flight = 0
+    nxt = 0
+    while True:
+        now = time.perf_counter() - t_start
+        if arrivals is not None:
+            while nxt < len(arrivals) and arrivals[nxt] <= now and arrivals[nxt] < window:
+                queue.append((nxt, arrivals[nxt]))
+                nxt += 1
+                offered_n += 1
+        else:
+            while now < window and in_flight + len(queue) < closed_conc:
+                queue.append((nxt, now))
+                nxt += 1
+        while queue:
+            i, t_arr = queue[0]
+            shape, tau, rho = reqs[i % len(reqs)]
+            r = srv.submit(shape, tau, rho, tag=i)
+            if r is None:
+                break
+            queue.pop(0)
+            start_t[i] = (t_arr, shape)
+            in_flight += 1
+            admitted += 1
+        for r, i in srv.poll():
+            t_arr, shape = start_t.pop(i)
+            code = srv.result(r)[0]
+            srv.release(r)
+            in_flight -= 1
+            if code != S.STILES_OK:
+                failed += 1
+                continue
+            done_n += 1
+            done_flops += flops[shape]
+            lat.append(time.perf_counter() - t_start - t_arr)
+        if now >= window:
+            not_admitted += len(queue)  # offered in the window, never admitted (memory full)
+            queue.clear()
+            if in_flight == 0 or now > window + 100.0:
+                break
+        time.sleep(0.0005)
+    elapsed = time.perf_counter() - t_start
+    status = srv.stop()
+    lat_ms = np.array(lat) * 1e3
+    return {"completed": done_n, "failed": failed, "admitted": admitted, "not_admitted": not_admitted,
+            "offered": offered_n if arrivals is not None else admitted,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+            "served_tflops": done_flops / elapsed / 1e12, "requests_per_s": done_n / elapsed,
+            "elapsed_s": elapsed, "kernel_status": S.strerror(status)}
+
+
 def run_serving(args, world, rank, local):
     """Request server: open-loop Poisson arrivals over a fixed window (queueing
     delay included in the latency), then a closed loop at fixed concurrency."""
@@ -487,71 +620,15 @@ def run_serving(args, world, rank, local):
         return [(int(rng.integers(0, len(pool))), float(rng.uniform(0.1, 10.0)), float(rng.uniform(0.5, 0.99)))
                 for _ in range(count)]
 
-    def run_phase(arrivals, reqs, window, closed_conc=0):
-        """arrivals: times (s) or None for the closed loop; returns stats."""
-        srv.start(window + 120.0)
-        queue, start_t, lat, done_flops, done_n, failed = [], {}, [], 0.0, 0, 0
-        admitted, offered_n, not_admitted = 0, 0, 0
-        t_start = time.perf_counter()
-        in_flight = 0
-        nxt = 0
-        while True:
-            now = time.perf_counter() - t_start
-            if arrivals is not None:
-                while nxt < len(arrivals) and arrivals[nxt] <= now and arrivals[nxt] < window:
-                    queue.append((nxt, arrivals[nxt]))
-                    nxt += 1
-                    offered_n += 1
-            else:
-                while now < window and in_flight + len(queue) < closed_conc:
-                    queue.append((nxt, now))
-                    nxt += 1
-            while queue:
-                i, t_arr = queue[0]
-                shape, tau, rho = reqs[i % len(reqs)]
-                r = srv.submit(shape, tau, rho, tag=i)
-                if r is None:
-                    break
-                queue.pop(0)
-                start_t[i] = (t_arr, shape)
-                in_flight += 1
-                admitted += 1
-            for r, i in srv.poll():
-                t_arr, shape = start_t.pop(i)
-                code = srv.result(r)[0]
-                srv.release(r)
-                in_flight -= 1
-                if code != S.STILES_OK:
-                    failed += 1
-                    continue
-                done_n += 1
-                done_flops += flops[shape]
-                lat.append(time.perf_counter() - t_start - t_arr)
-            if now >= window:
-                not_admitted += len(queue)  # offered in the window, never admitted (memory full)
-                queue.clear()
-                if in_flight == 0 or now > window + 100.0:
-                    break
-            time.sleep(0.0005)
-        elapsed = time.perf_counter() - t_start
-        status = srv.stop()
-        lat_ms = np.array(lat) * 1e3
-        return {"completed": done_n, "failed": failed, "admitted": admitted, "not_admitted": not_admitted,
-                "offered": offered_n if arrivals is not None else admitted,
-                "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
-                "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
-                "served_tflops": done_flops / elapsed / 1e12, "requests_per_s": done_n / elapsed,
-                "elapsed_s": elapsed, "kernel_status": S.strerror(status)}
-
     reqs = draw(200000)
     arr = np.cumsum(rng.exponential(1.0 / 200.0, size=int(200 * args.serve_window * 1.2) + 10))
     offered = sum(flops[reqs[i][0]] for i in range(len(arr)) if arr[i] < args.serve_window) / args.serve_window
-    open_loop = run_phase(list(arr), reqs, args.serve_window)
+    open_loop = serve_phase(S, srv, flops, list(arr), reqs, args.serve_window)
     open_loop["offered_tflops"] = offered / 1e12
     open_loop["offered_requests_per_s"] = float(np.sum(arr < args.serve_window)) / args.serve_window
     closed_runs = []
     for conc in [int(c) for c in str(args.serve_concurrency).split(",")]:
-        r = run_phase(None, reqs, args.serve_window, closed_conc=conc)
+        r = serve_phase(S, srv, flops, None, reqs, args.serve_window, closed_conc=conc)
         r["concurrency"] = conc
         closed_runs.append(r)
     closed = max(closed_runs, key=lambda r: r["requests_per_s"])
@@ -570,6 +647,142 @@ def run_serving(args, world, rank, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def cached_codes(shapes, prec):
+    """Tuning codes of the shipped autotuner cache for these shapes (0 where
+    the cache has no entry: the compact records never start a tuning run)."""
+    from paper_2504_19171_gb300 import autotune as AT
+    tuner = AT.Autotuner(AT.default_cache_path())
+    return [int(tuner.cache.get(AT.key_of(b, w, a, prec), {}).get("code", 0)) for (_, b, w, a) in shapes]
+
+
+def compact_batched(S, W, dev, stream, args) -> dict:
+    """A compact form of the batched workload for the default line: the first
+    ``args.compact_count`` matrices of the uneven draw (same distribution and
+    values as the 64-matrix workload), one graph launch per batch in FP64,
+    EMU64 and FP32X with the autotuner's cached codes, against plain FP64
+    per-matrix launches; matrices/s, error of each variant against the FP64
+    batch, and the roofline fraction of each batched launch."""
+    import torch
+    count = args.compact_count
+    shapes = W.batch_shapes(count, seed=BATCH["seed"])
+    peaks = measured_peaks()
+    steps, warmup = 2, 1
+    A, mask, S64, res = None, None, None, {}
+    launches = 0
+    for name, prec in (("fp64", S.STILES_FP64), ("emu64", S.STILES_EMU64), ("fp32x", S.STILES_FP32X)):
+        codes = cached_codes(shapes, prec)
+        bt = S.StilesBatch(shapes, device=str(dev), precision=prec, tuning=codes, wait_budget_s=60)
+        try:
+            if A is None:
+                A = torch.empty(bt.doubles, dtype=torch.float64, device=dev)
+                for m, sh in enumerate(shapes):
+                    W.random_arrowhead_packed(*sh, 1000 + m, A[bt.off[m]:bt.off[m] + bt.layouts[m].doubles])
+                mask = used_mask(bt.layouts, bt.off, bt.doubles, dev)
+            bt.A = A
+            stats = S.stiles_batch_stats(bt.h)
+            for _ in range(warmup):
+                bt.factor_selinv(stream)
+            torch.cuda.synchronize(dev)
+            bad = [m for m in range(count) if bt.status(m)[0] != S.STILES_OK]
+            if bad:
+                res[name] = {"status": f"matrices {bad} failed"}
+                continue
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                bt.factor_selinv(stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            launches += warmup + steps
+            t = e0.elapsed_time(e1) / 1e3 / steps
+            r = {"matrices_per_s": count / t, "tflops": stats["flops"] / t / 1e12, "ms_per_batch": 1e3 * t,
+                 "tuning": sorted(set(codes))}
+            if name == "fp64":
+                S64 = bt.S.clone()
+                r["roofline"] = {"bound": "alu", "achieved": r["tflops"], "peak": FP64_PEAK_TFLOPS,
+                                 "unit": "TFLOP/s", "frac": r["tflops"] / FP64_PEAK_TFLOPS}
+            else:
+                errs = []
+                for m in range(count):
+                    sl = slice(bt.off[m], bt.off[m] + bt.layouts[m].doubles)
+                    mk = mask[sl]
+                    errs.append(float((bt.S[sl][mk] - S64[sl][mk]).abs().max() / S64[sl][mk].abs().max()))
+                r["sigma_err_vs_fp64"] = max(errs)
+                r["roofline"] = variant_roofline(name, stats["flops"], stats["flops_lowered"], t, peaks)
+            res[name] = r
+        finally:
+            bt.A = None
+            bt.close()
+            del bt
+            torch.cuda.empty_cache()
+    # plain FP64 per-matrix form: one handle and one launch per matrix, in sequence
+    off = [0]
+    for sh in shapes:
+        lay = S.PackedLayout(*sh)
+        off.append(off[-1] + -(-lay.doubles // 32) * 32)
+    t_solo = 0.0
+    for m, sh in enumerate(shapes):
+        st = S.Stiles(*sh, device=str(dev))
+        st.A = A[off[m]:off[m] + st.doubles]
+        st.factor_selinv(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.factor_selinv(stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        launches += 2
+        t_solo += e0.elapsed_time(e1) / 1e3
+        st.A = None
+        st.close()
+    del A, mask, S64
+    torch.cuda.empty_cache()
+    solo = count / t_solo
+    return {"config": dict(BATCH, count=count, note=f"the first {count} matrices of the seed-0 draw"),
+            "fp64_per_matrix": {"matrices_per_s": solo, "seconds": t_solo},
+            **res,
+            "vs_fp64_per_matrix": {k: v["matrices_per_s"] / solo for k, v in res.items() if "matrices_per_s" in v},
+            "gpu_launches": launches}
+
+
+def compact_serving(S, W, dev, args) -> dict:
+    """A compact form of the served workload for the default line: a pool of
+    the first 16 shapes of the uneven draw (fixed pattern and base values per
+    shape, per-request (tau, rho) as in the served workload), closed loops of
+    ``args.compact_window`` seconds with 1 and 16 requests in flight, in EMU64
+    and FP64: p50 / p99 latency and requests/s."""
+    import numpy as np
+    import torch
+    pool = W.batch_shapes(16, seed=0)
+    flops = [S.stiles_plan_stats(*sh, S.PLAN_FUSED, 152)["flops"] for sh in pool]
+    out = {"config": dict(SERVE, pool="the first 16 shapes of the batched draw (seed 0)",
+                          window_s=args.compact_window, data_arena_gb=64, in_flight=[1, 16])}
+    for name, prec in (("emu64", S.STILES_EMU64), ("fp64", S.STILES_FP64)):
+        rng = np.random.default_rng(1)
+        reqs = [(int(rng.integers(0, len(pool))), float(rng.uniform(0.1, 10.0)), float(rng.uniform(0.5, 0.99)))
+                for _ in range(20000)]
+        srv = S.StilesServer(pool, int(64 * 2**30), max_requests=64, precision=prec,
+                             tuning=cached_codes(pool, prec), device=str(dev))
+        try:
+            for m, sh in enumerate(pool):
+                d, n = srv.shape_doubles(m)
+                base = torch.zeros(d, dtype=torch.float64, device=dev)
+                rb, ra = W.sweep_base_packed(*sh, 2000 + m, base)
+                srv.set_base(m, base, rb, ra)
+                del base
+            torch.cuda.synchronize(dev)
+            runs = {}
+            for conc in (1, 16):
+                r = serve_phase(S, srv, flops, None, reqs, args.compact_window, closed_conc=conc)
+                runs[f"in_flight_{conc}"] = {k: r[k] for k in ("p50_ms", "p99_ms", "requests_per_s", "served_tflops",
+                                                               "completed", "failed", "kernel_status")}
+            out[name] = runs
+        finally:
+            srv.close()
+            torch.cuda.empty_cache()
+    out["gpu_launches"] = 4
+    return out
 
 
 def run_ours(args, world, rank, local):
@@ -655,6 +868,7 @@ def run_ours(args, world, rank, local):
         e2e_value = whole_job_rate(world, e2e_steps, flops, te) / 1e12
 
     args.tuner = tuner
+    args.peaks = measured_peaks()
     variants = None if args.no_variants else measure_variants(S, st, stream, dev, flops, logdet, args)
 
     achieved = flops / (sum(per_launch) / len(per_launch)) / 1e12
@@ -665,6 +879,19 @@ def run_ours(args, world, rank, local):
     sha = kernel_sources_sha()
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["sources_sha"] == sha and args.band == WORKLOAD["w"] and \
         args.nt == WORKLOAD["nt"] else None
+    # algorithmic bytes of one launch: read A, write L, read L back, write Sigma
+    alg_bytes = 4 * 8 * st.doubles
+    st.close()
+    del A_host, S_host
+    dgemm = None
+    if not args.no_dgemm:
+        dclk = ClockSampler(dev.index if dev.index is not None else 0).start()
+        dgemm = measure_fp64_gemm(dev)
+        dgemm["clocks"] = dclk.stop()
+    extra = {}
+    if not args.no_compact and world == 1:
+        extra["batched"] = compact_batched(S, W, dev, stream, args)
+        extra["serving"] = compact_serving(S, W, dev, args)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -684,9 +911,18 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "stiles::persistent_kernel (FP64 pipe)",
-                     "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 pipe; tcgen05 has no f64 kind)"},
+                     "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 pipe; tcgen05 has no f64 kind)",
+                     "algorithmic_bytes": alg_bytes,
+                     "traffic_over_algorithmic": traffic / alg_bytes if traffic else None,
+                     "traffic_note": "measured DRAM bytes above the algorithmic ones are re-reads of L, U and "
+                                     "Sigma blocks by later tasks (the FP64 path is bound by the FP64 pipe, not HBM)",
+                     "peak_measured": None if dgemm is None else {
+                         "dgemm_tflops": dgemm["tflops"], "frac_of_dgemm": achieved / dgemm["tflops"],
+                         "how": dgemm["how"], "clocks": dgemm["clocks"]}},
+        **extra,
     }
-    st.close()
+    if extra:
+        line["gpu_launches"] += sum(v.get("gpu_launches", 0) for v in extra.values() if isinstance(v, dict))
     if args.band != WORKLOAD["w"]:
         line["config"]["workload"] += f"_band{args.band}"
         line["config"]["w"] = args.band
@@ -814,6 +1050,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the EMU64 / FP32X lines")
     ap.add_argument("--variant-steps", type=int, default=2)
+    ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM reference rate")
+    ap.add_argument("--no-compact", action="store_true",
+                    help="skip the compact batched and served records of the default line")
+    ap.add_argument("--compact-count", type=int, default=16, help="matrices in the compact batched record")
+    ap.add_argument("--compact-window", type=float, default=8.0, help="seconds per closed loop of the compact "
+                    "served record")
     ap.add_argument("--band", type=int, default=WORKLOAD["w"],
                     help="tile bandwidth: Q_t is replaced by Q_t^band (default 1; 4 raises the arithmetic intensity)")
     ap.add_argument("--nt", type=int, default=WORKLOAD["nt"],

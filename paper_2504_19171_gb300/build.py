@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libstiles.so")
 SOURCES = ["stiles_kernel.cu", "stiles_api.cu", "stiles_server.cu", "plan.cpp"]
-HEADERS = ["plan.h", "stiles_device.h"]
+HEADERS = ["plan.h", "stiles_device.h", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -83,7 +83,7 @@ struct Builder {
     if (t.prec != PREC_FP64) flops_lowered += sym_block ? 0.5 * f : f;
     sym_block = false;
     if (t.pmode == PM_TRI3) f *= 0.75;
-    if (t.prec == PREC_EMU64) f /= 10.0;   // measured order of the emulated-FP64 speed-up per block
+    if (t.prec == PREC_EMU64) f /= 10.0;   // order of the emulated-FP64 speed-up per block
     if (t.prec == PREC_FP32X) f /= 25.0;
     int id = (int)tasks.size();
     tasks.push_back(t);
@@ -127,13 +127,14 @@ struct Builder {
     else if (mode == 1) split(t, PM_ROWS2);
   }
 
-  // Mark a bulk product task with the plan's reduced precision. The emulated
-  // FP64 kernel works on sub-tiles of at most 32 x 32: blocks that are not
+  // Mark a bulk product task with the plan's reduced precision. The tensor-
+  // core digit products work on sub-tiles of at most 32 x 32 (four digit
+  // planes of 32 rows fill the 128 rows of one MMA): blocks that are not
   // already split that way run as a grid of such tiles.
   void lower_precision(Task& t) const {
     if (s.prec == PREC_FP64) return;
     t.prec = (uint8_t)s.prec;
-    if (s.prec == PREC_EMU64 && t.pmode != PM_QUAD4 && t.pmode != PM_TRI3) {
+    if (t.pmode != PM_QUAD4 && t.pmode != PM_TRI3) {
       const int pr = t.m > 32 ? 2 : 1, pc = t.n > 32 ? 2 : 1;
       t.pmode = PM_TILE32;
       t.parts = (uint8_t)(pr * pc);

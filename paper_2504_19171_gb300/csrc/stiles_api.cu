@@ -238,6 +238,7 @@ static int launch(stiles_t h, int kind, const double* A, double* L, double* S, v
   p.buf[BUF_W] = (double*)scr;
   p.smirror = smirror;
   p.budget_ns = h->budget_ns;
+  p.use_tc = h->s.prec != PREC_FP64;
   p.trace = h->dtrace;
   if (h->dtrace && cudaMemsetAsync(h->dtrace, 0, 16 * sizeof(unsigned long long) * h->trace_tasks, st) != cudaSuccess)
     return STILES_ERR_CUDA;
@@ -698,6 +699,7 @@ static int build_batch_graph(stiles_batch* h, const double* A, double* L, double
   p.buf[BUF_S] = S;
   p.buf[BUF_W] = (double*)scr;
   p.budget_ns = h->budget_ns;
+  p.use_tc = h->prec != PREC_FP64;
   p.trace = nullptr;
   p.buf_len = h->off[h->count];
   cudaGraph_t g = nullptr;

@@ -125,6 +125,7 @@ struct KParams {
   unsigned long long* trace;  // optional: 4 words per task (claim, ready, end ns; sm/cta/op), or null
   long long buf_len;          // doubles in each of buf[0..3] (self-checking builds)
   int serve;                  // 1: request server (rings and inbox instead of the static buckets)
+  int use_tc;                 // 1: the plan has reduced-precision products (tensor memory and barriers held)
   ServeDev sv;
 };
 

@@ -19,8 +19,9 @@
 // shared memory (L2-only loads, so data published by other SMs is never read
 // from a stale L1 line) and accumulates up to a 64 x 64 block in registers
 // (4 x 8 per thread). The reduced-precision modes replace the products of
-// the bulk tasks: emulated FP64 (bf16 digit products on the tensor cores)
-// and FP32-class (FP32 FMA). In the end-to-end call the matrix may live in
+// the bulk tasks by split-precision digit products on the tensor cores
+// (tcgen05 MMAs from shared memory into tensor memory): 8 digits per operand
+// for emulated FP64, 4 for the FP32-class mode. In the end-to-end call the matrix may live in
 // page-locked host memory (read over the host link by the tasks that first
 // load each block) and every final Sigma write is repeated into a host
 // buffer, so the transfers overlap the computation.
@@ -33,6 +34,7 @@
 
 #include "plan.h"
 #include "stiles_device.h"
+#include "tcgen05.cuh"
 
 namespace stiles {
 
@@ -529,135 +531,60 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
   }
 }
 
-// FP32-class products: operands rounded to FP32 while staged, FP32 FMA
-// accumulation, result returned in FP64 (same thread mapping as accumulate).
-template <int TM, int TN>
-__device__ __forceinline__ void accumulate_f32(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[TM][TN],
-                                               double* smem) {
-  constexpr int RM = 16 * TM, CN = 8 * TN, LF = FB + 1;
-  float* As = reinterpret_cast<float*>(smem);
-  float* Bs = As + KC * LF;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float f[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) f[i][j] = 0.0f;
-  for (int s = 0; s < tk.nseg; ++s) {
-    const Seg g = load_seg(p, tk.seg0 + s);
-    const bool ta = g.trans & 1, tb = g.trans & 2;
-    const double* A = resolve(p, g.a) + (ta ? (int64_t)sb.r0 * g.lda : (int64_t)sb.r0);
-    const double* B = resolve(p, g.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * g.ldb);
-    for (int k0 = 0; k0 < g.k; k0 += KC) {
-      const int kc = min(KC, g.k - k0);
-      // all loads of this thread for the chunk are in flight before any is stored
-      constexpr int NA = RM * KC / NTHREADS, NB = CN * KC / NTHREADS;
-      float fa[NA], fb[NB];
-#pragma unroll
-      for (int u = 0; u < NA; ++u) {
-        const int e = tid + u * NTHREADS;
-        int i, kk;
-        if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
-        fa[u] = (i < sb.rm && kk < kc)
-                    ? (float)__ldcg(ta ? A + (int64_t)(k0 + kk) + (int64_t)i * g.lda : A + (int64_t)i + (int64_t)(k0 + kk) * g.lda)
-                    : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < NB; ++u) {
-        const int e = tid + u * NTHREADS;
-        int j, kk;
-        if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
-        fb[u] = (j < sb.cn && kk < kc)
-                    ? (float)__ldcg(tb ? B + (int64_t)j + (int64_t)(k0 + kk) * g.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * g.ldb)
-                    : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < NA; ++u) {
-        const int e = tid + u * NTHREADS;
-        int i, kk;
-        if (!ta) { i = e % RM; kk = e / RM; } else { kk = e % KC; i = e / KC; }
-        As[kk * LF + i] = fa[u];
-      }
-#pragma unroll
-      for (int u = 0; u < NB; ++u) {
-        const int e = tid + u * NTHREADS;
-        int j, kk;
-        if (tb) { j = e % CN; kk = e / CN; } else { kk = e % KC; j = e / KC; }
-        Bs[kk * LF + j] = fb[u];
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < KC; ++kk) {
-        float a[TM], b[TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk * LF + tx + 16 * i];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[kk * LF + ty + 8 * j];
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) f[i][j] = fmaf(a[i], b[j], f[i][j]);
-      }
-      __syncthreads();
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = (double)f[i][j];
-}
-
-// ---- emulated FP64 on the tensor cores (split-precision integer digits) --
+// ---- split-precision block products on the tensor cores (tcgen05) -------
 //
-// Error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump: for one
-// segment, every row i of op(A) gets the exponent E_i of its largest entry
-// and every column j of op(B) the exponent F_j; each entry becomes a 56-bit
-// fixed-point integer relative to that exponent (the largest entry keeps all
-// 53 bits of its significand), cut into EMU_S = 7 unsigned 8-bit digits
-// carrying the entry's sign, which bf16 holds exactly. A product of two digits
-// is an exact 16-bit integer; a sum of at most 7 x 32 of them stays below
-// 2^24, so the FP32 tensor-core accumulation of one K chunk is exact and is
-// moved into an int32 accumulator per level L = t + u (digit weights 2^-8t,
-// 2^-8u). Levels L <= EMU_S - 1 are kept (the dropped ones and the operand
-// truncation weigh about (EMU_S + 1) 2^-56 of max|row| max|column| per
-// product), and the levels are recombined exactly in 128-bit integers, then
-// scaled by 2^(E_i + F_j).
-constexpr int EMU_S = 7;
-constexpr int EMU_KP = 36;  // padded digit-row length (bf16) in shared memory
-// An operand of biased exponent e <= emax has the fixed-point value m 2^(e - emax + 8 EMU_S - 53);
-// the product of two then carries the scale 2^(E_i + F_j - kEmuScale).
-constexpr int kEmuScale = 2 * (1075 + 8 * EMU_S - 53);
-static_assert(2 * EMU_S * 32 * EMU_KP * 2 <= 2 * KC * LDS * 8, "digit panels must fit the staging region");
-static_assert(EMU_S * 8 * NTHREADS * 4 + 64 * 4 <= FB * LDS * 8, "level sums must fit the block region");
-static_assert(EMU_S * 32 * 255 * 255 < (1 << 24), "one K chunk of a level must be exact in FP32");
+// Error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump. For one
+// task part (at most 32 x 32 outputs) every row i of op(A) gets the biased
+// exponent E_i of its largest entry over all the task's segments and every
+// column j of op(B) the exponent F_j. Each entry becomes a signed fixed-point
+// integer X relative to that exponent, |X| < 2^(7S-2) (the largest entry of
+// the row keeps its 53-bit significand when S = 8; the others are rounded to
+// the same unit), written as S balanced base-128 digits d_t in [-64, 63],
+// X = sum_t d_t 128^(S-1-t), which bf16 holds exactly. A digit product is an
+// integer of magnitude at most 2^12; products of levels L = t + u <= S - 1
+// are kept. S = 8 (56 bits) is the emulated-FP64 mode, S = 4 (28 bits) the
+// FP32-class mode.
+//
+// Tensor-core layout. D has M = 128 rows, made from a 32-row part by
+// stacking four digit planes of A: stack g (g < G = S / 4) holds plane
+// g + G p in rows 32 p + i (p = 0..3). The B planes are concatenated along
+// N ([B_0 | B_1 | ... | B_{S-1}], 32 columns each). Stack g is multiplied by
+// the first 32 (S - g) columns of that concatenation into TMEM columns from
+// 32 g on, so TMEM cell (lane block p, column block c) collects the plane
+// pairs (g + G p, c - g), all of one level L = G p + c. A cell receives at
+// most G pairs per K step: its FP32 sums are integers below 2^24, hence
+// exact, for up to 2^24 / (G 2^12) = 4096 / G of K (2048 for S = 8). Before
+// that much K has been accumulated (or at the end of the task) the cells of
+// levels <= S - 1 are read -- warp p reads lane block p -- and combined per
+// output: exactly in two 64-bit halves for S = 8, in FP32 for S = 4. The
+// result, scaled by 2^(E_i + F_j - bias), is added to the part's FP64 value.
+// Non-finite operands (biased exponent 0x7ff) make their row or column NaN.
+
+constexpr int TC_KS = 32;           // K per staging buffer (two MMA K steps)
+constexpr int TC_COLS = 256;        // TMEM columns per CTA (two CTAs per SM share 512)
+constexpr int TC_STAGE_BYTES_MAX = 2 * 32 * 8 * TC_KS * 2;  // A and B digit planes of S = 8
+// shared memory of a tensor part: two staging buffers, the row / column
+// exponents, then the part's FP64 result (32 x 33 doubles)
+constexpr int TC_EXP_OFF = 2 * TC_STAGE_BYTES_MAX;
+constexpr int TC_RES_OFF = TC_EXP_OFF + 64 * 4;
+constexpr int TC_SMEM_BYTES = TC_RES_OFF + 32 * 33 * 8;
+
+// Per-CTA state of the tensor path (static shared memory of the kernel).
+struct TcShared {
+  uint64_t mbar[2];      // completion barriers of the two staging buffers
+  uint32_t ncommit[2];   // commits issued to each barrier so far (this launch)
+  uint32_t tmem;         // TMEM base address of this CTA's TC_COLS columns
+};
 
 __device__ __forceinline__ int biased_exp(double v) {
   return (int)((__double_as_longlong(v) >> 52) & 0x7ff);
 }
 
-// The EMU_S digits of v relative to the biased exponent emax (>= that of v),
-// as bf16 bit patterns (sign applied to every digit).
-__device__ __forceinline__ void emu_digits(double v, int emax, uint16_t (&d)[EMU_S]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((bits >> 52) & 0x7ff);
-  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-  const int shift = emax - (e ? e : 1) - (8 * EMU_S - 53);  // >= -(8 EMU_S - 53)
-  const unsigned long long X = shift >= 64 ? 0ull : shift >= 0 ? (m >> shift) : (m << -shift);  // < 2^(8 EMU_S)
-  const uint16_t sgn = (uint16_t)((bits >> 48) & 0x8000u);
-#pragma unroll
-  for (int t = 0; t < EMU_S; ++t) {
-    const unsigned dt = (unsigned)(X >> (8 * (EMU_S - 1 - t))) & 0xffu;
-    // exact float of an 8-bit integer, then its upper 16 bits (= its bf16)
-    const float f = __uint_as_float(0x4B000000u | dt) - 8388608.0f;
-    d[t] = dt ? (uint16_t)((__float_as_uint(f) >> 16) | sgn) : (uint16_t)0;
-  }
-}
-
-// out[i] = largest biased exponent over k < K of element (i, k) of a panel of
-// n <= 32 vectors: element (i, k) sits at P[i + k ld] when `along_i` (the
-// vectors' index is the contiguous one), else at P[k + i ld]. Loads follow
-// the contiguous dimension; out[] gets every i < 32 (0 beyond n).
-__device__ __forceinline__ void emu_max_exp(const double* P, int ld, bool along_i, int n, int K, int* out) {
+// out[i] = max(out[i], largest biased exponent over k < K of element (i, k))
+// of a panel of n <= 32 vectors: element (i, k) sits at P[i + k ld] when
+// `along_i` (the vectors' index is the contiguous one), else at P[k + i ld].
+// Loads follow the contiguous dimension. Ends with a block barrier.
+__device__ __forceinline__ void max_exp_into(const double* P, int ld, bool along_i, int n, int K, int* out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (along_i) {  // lanes over i, warps over k
     int mx = 0;
@@ -666,8 +593,7 @@ __device__ __forceinline__ void emu_max_exp(const double* P, int ld, bool along_
     __shared__ int part[4][32];
     part[warp][lane] = mx;
     __syncthreads();
-    if (warp == 0) out[lane] = max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane]));
-    __syncthreads();
+    if (warp == 0) out[lane] = max(out[lane], max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane])));
   } else {  // one warp per vector, lanes over k
     for (int i = warp; i < 32; i += 4) {
       int mx = 0;
@@ -675,156 +601,273 @@ __device__ __forceinline__ void emu_max_exp(const double* P, int ld, bool along_
         for (int k = lane; k < K; k += 32) mx = max(mx, biased_exp(__ldcg(P + k + (int64_t)i * ld)));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) out[i] = mx;
+      if (lane == 0) out[i] = max(out[i], mx);
     }
+  }
+  __syncthreads();
+}
+
+// Signed fixed-point value of v relative to the biased exponent emax of its
+// row or column (emax >= its own), rounded to nearest: the row maximum maps
+// to [2^(BITS-1), 2^BITS).
+template <int BITS>
+__device__ __forceinline__ long long fixed_point(double v, int emax) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  const long long m = (long long)((bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull));
+  const int sh = max(emax, 1) - max(e, 1) + 53 - BITS;  // >= 53 - BITS
+  long long X;
+  if (sh < 0) X = m << -sh;
+  else if (sh == 0) X = m;
+  else if (sh < 63) X = (m + (1ll << (sh - 1))) >> sh;
+  else X = 0;
+  return (bits >> 63) ? -X : X;
+}
+
+// The S digits of a pair of K-adjacent values (v0 at k, v1 at k + 1) as
+// packed bf16 pairs: w[t] = bf16(d_t(v0)) | bf16(d_t(v1)) << 16.
+template <int S>
+__device__ __forceinline__ void digit_pairs(double v0, double v1, int emax, uint32_t (&w)[S]) {
+  constexpr int BITS = 7 * S - 2;
+  // C = sum_t 64 128^t: X + C has base-128 digits d_t + 64 in [0, 127]
+  constexpr unsigned long long C = 0x0081020408102040ull >> (7 * (8 - S));
+  const unsigned long long y0 = (unsigned long long)(fixed_point<BITS>(v0, emax) + (long long)C);
+  const unsigned long long y1 = (unsigned long long)(fixed_point<BITS>(v1, emax) + (long long)C);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    const int s = 7 * (S - 1 - t);
+    // exact float of (field - 64): 2^23 + field, minus 2^23 + 64; its bf16 is its upper half
+    const float f0 = __uint_as_float(0x4B000000u | (unsigned)((y0 >> s) & 0x7f)) - 8388672.0f;
+    const float f1 = __uint_as_float(0x4B000000u | (unsigned)((y1 >> s) & 0x7f)) - 8388672.0f;
+    w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
   }
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// Byte offset of element (row, k) (k even: a packed pair) in a staging
+// operand of canonical K-major core matrices: 8 rows x 8 K per 128 bytes,
+// TC_KS / 8 core matrices along K per 8-row group.
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+  return (uint32_t)((((row >> 3) * (TC_KS / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+constexpr uint32_t TC_LBO = 128;                 // K-adjacent core matrices
+constexpr uint32_t TC_SBO = (TC_KS / 8) * 128;   // 8-row groups
+
+// Panel element owned by slot q (0..3) of this thread, for a stage of 32
+// vectors x TC_KS: vector index `vi` and the even K offset `kk` of its pair.
+// When the vectors are the contiguous dimension, lanes run over vectors;
+// otherwise over K pairs.
+__device__ __forceinline__ void tc_slot(bool along_vec, int q, int& vi, int& kk) {
+  const int tid = threadIdx.x;
+  if (along_vec) {
+    vi = tid & 31;
+    kk = 2 * ((tid >> 5) + 4 * q);
+  } else {
+    kk = 2 * (tid & 15);
+    vi = (tid >> 4) + 8 * q;
+  }
 }
 
-// Sub-tile of at most 32 x 32; returns the products in the accumulate<2,4>
-// thread mapping (through shared memory).
-__device__ void accumulate_emu(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[2][4], double* smem) {
-  uint16_t* Ad = reinterpret_cast<uint16_t*>(smem);  // [EMU_S][32][EMU_KP]
-  uint16_t* Bd = Ad + EMU_S * 32 * EMU_KP;            // [EMU_S][32][EMU_KP]
-  int* rexp = reinterpret_cast<int*>(smem + 2 * KC * LDS);  // X region: exponents, level sums, result
+// Bounded wait for phase `parity` of a staging barrier (all threads).
+__device__ bool tc_wait(const KParams& p, uint32_t mbar, uint32_t parity) {
+  if (tc::mbar_test(mbar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!tc::mbar_test(mbar, parity)) {
+    if (gtimer() - t0 > (unsigned long long)p.budget_ns) {
+      raise_timeout(p, -3);
+      return false;
+    }
+  }
+  return true;
+}
+
+// acc (accumulate<2,4> thread mapping: rows tx + 16 i, columns ty + 8 jj) =
+// sum over the task's segments of op(A) op(B) for the sub-tile sb (<= 32 x
+// 32), through S-digit products on the tensor cores (see above).
+template <int S>
+__device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[2][4], double* smem,
+                              TcShared& ts) {
+  constexpr int G = S / 4;                 // stacks of four A planes
+  constexpr int BITS = 7 * S - 2;
+  constexpr int KMAX = 4096 / G;           // K accumulated exactly in a TMEM cell
+  constexpr int ROWS = 32 * S;             // rows of the A stacks and of the B concatenation
+  constexpr uint32_t OPB = ROWS * TC_KS * 2;  // bytes of one operand in a stage
+  // k2 = E_i + F_j - kScale: X_a X_b summed over the kept levels is
+  // 2^(7 (S - 1)) V with V = sum_L S_L 2^(7 (S - 1 - L))
+  constexpr int kScale = 2044 + 2 * BITS - 7 * (S - 1);
+  static_assert(S == 4 || S == 8, "digit counts of the two modes");
+  uint8_t* stage = reinterpret_cast<uint8_t*>(smem);
+  int* rexp = reinterpret_cast<int*>(stage + TC_EXP_OFF);
   int* cexp = rexp + 32;
-  int* lev = cexp + 32;  // [EMU_S * 8][NTHREADS] int32 level accumulators (per thread, conflict-free)
-  double* R = smem + 2 * KC * LDS + 32;  // 32 x 33 result scatter (after the level sums are consumed)
+  // the part's result, row lane, column 4 js + warp owned by thread (warp, lane)
+  double* R = reinterpret_cast<double*>(stage + TC_RES_OFF);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, tq = lane & 3, wr = warp & 1, wc = warp >> 1;
-  double res[2][4];  // rows 16 wr + g + 8 h (h = q >> 1), cols 16 wc + 8 j + 2 tq + (q & 1)
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) res[j][q] = 0.0;
+  // exponents of the rows of op(A) and columns of op(B) over all segments
+  if (tid < 64) rexp[tid] = 0;
+  __syncthreads();
   for (int s = 0; s < tk.nseg; ++s) {
     const Seg gs = load_seg(p, tk.seg0 + s);
     const bool ta = gs.trans & 1, tb = gs.trans & 2;
     const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
     const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
-    // exponents of the largest entry of every row of op(A) / column of op(B),
-    // read along each operand's contiguous dimension
-    emu_max_exp(A, gs.lda, !ta, sb.rm, gs.k, rexp);
-    emu_max_exp(B, gs.ldb, tb, sb.cn, gs.k, cexp);
-    __syncthreads();
-    static_assert((long long)EMU_S * 4096 * 255 * 255 < (1ll << 31), "level sums over 4096 of K must fit int32");
-    // int32 level sums stay exact for EMU_S * 4096 * 255^2 < 2^31: recombine every 4096 of K
-    for (int kb = 0; kb < gs.k; kb += 4096) {
-      const int kend = min(gs.k, kb + 4096);
+    max_exp_into(A, gs.lda, !ta, sb.rm, gs.k, rexp);
+    max_exp_into(B, gs.ldb, tb, sb.cn, gs.k, cexp);
+  }
 #pragma unroll
-      for (int x = 0; x < EMU_S * 8; ++x) lev[x * NTHREADS + tid] = 0;
-      for (int k0 = kb; k0 < kend; k0 += KC) {
-        const int kc = min(KC, kend - k0);
-        // stage the digits of op(A)[0:32, k0:k0+32] and op(B)[k0:k0+32, 0:32]:
-        // all 16 loads of this thread are issued before any is used
-        constexpr int NE = 32 * KC / NTHREADS;
-        double va[NE], vb[NE];
+  for (int js = 0; js < 8; ++js) R[lane * 33 + 4 * js + warp] = 0.0;
+  int nstage = 0, kacc = 0;
+  const uint32_t mb0 = tc::smem_addr(&ts.mbar[0]), mb1 = tc::smem_addr(&ts.mbar[1]);
+  for (int s = 0; s < tk.nseg; ++s) {
+    const Seg gs = load_seg(p, tk.seg0 + s);
+    const bool ta = gs.trans & 1, tb = gs.trans & 2;
+    const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
+    const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
+    for (int k0 = 0; k0 < gs.k; k0 += TC_KS) {
+      const int kc = min(TC_KS, gs.k - k0);
+      const int buf = nstage & 1;
+      uint8_t* sa = stage + buf * TC_STAGE_BYTES_MAX;
+      uint8_t* sbuf = sa + OPB;
+      // the MMAs that last read this buffer (two stages ago) must be done
+      // (a wait that runs out of budget ends the part on every thread at the barrier below)
+      const bool ok = nstage < 2 || tc_wait(p, buf ? mb1 : mb0, (ts.ncommit[buf] - 1) & 1);
+      // op(A) rows: digit t of row i goes to stack row 128 (t % G) + 32 (t / G) + i
 #pragma unroll
-        for (int u = 0; u < NE; ++u) {
-          const int e = tid + u * NTHREADS;
-          int i, kk;
-          if (!ta) { i = e & 31; kk = e >> 5; } else { kk = e & 31; i = e >> 5; }
-          va[u] = (i < sb.rm && kk < kc)
-                      ? __ldcg(ta ? A + (int64_t)(k0 + kk) + (int64_t)i * gs.lda : A + (int64_t)i + (int64_t)(k0 + kk) * gs.lda)
-                      : 0.0;
+      for (int q = 0; q < 4 && ok; ++q) {
+        int i, kk;
+        tc_slot(!ta, q, i, kk);
+        double v0 = 0.0, v1 = 0.0;
+        if (i < sb.rm) {
+          const double* P = ta ? A + (int64_t)(k0 + kk) + (int64_t)i * gs.lda : A + (int64_t)i + (int64_t)(k0 + kk) * gs.lda;
+          const int64_t step = ta ? 1 : gs.lda;
+          if (kk < kc) v0 = __ldcg(P);
+          if (kk + 1 < kc) v1 = __ldcg(P + step);
         }
+        uint32_t w[S];
+        digit_pairs<S>(v0, v1, rexp[i], w);
 #pragma unroll
-        for (int u = 0; u < NE; ++u) {
-          const int e = tid + u * NTHREADS;
-          int j, kk;
-          if (tb) { j = e & 31; kk = e >> 5; } else { kk = e & 31; j = e >> 5; }
-          vb[u] = (j < sb.cn && kk < kc)
-                      ? __ldcg(tb ? B + (int64_t)j + (int64_t)(k0 + kk) * gs.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * gs.ldb)
-                      : 0.0;
+        for (int t = 0; t < S; ++t)
+          *reinterpret_cast<uint32_t*>(sa + tc_off(128 * (t % G) + 32 * (t / G) + i, kk)) = w[t];
+      }
+      // op(B) columns: digit u of column j goes to row 32 u + j
+#pragma unroll
+      for (int q = 0; q < 4 && ok; ++q) {
+        int j, kk;
+        tc_slot(tb, q, j, kk);
+        double v0 = 0.0, v1 = 0.0;
+        if (j < sb.cn) {
+          const double* P = tb ? B + (int64_t)j + (int64_t)(k0 + kk) * gs.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * gs.ldb;
+          const int64_t step = tb ? gs.ldb : 1;
+          if (kk < kc) v0 = __ldcg(P);
+          if (kk + 1 < kc) v1 = __ldcg(P + step);
         }
+        uint32_t w[S];
+        digit_pairs<S>(v0, v1, cexp[j], w);
 #pragma unroll
-        for (int u = 0; u < NE; ++u) {
-          const int e = tid + u * NTHREADS;
-          int i, kk;
-          if (!ta) { i = e & 31; kk = e >> 5; } else { kk = e & 31; i = e >> 5; }
-          uint16_t d[EMU_S];
-          emu_digits(va[u], rexp[i], d);
+        for (int t = 0; t < S; ++t) *reinterpret_cast<uint32_t*>(sbuf + tc_off(32 * t + j, kk)) = w[t];
+      }
+      tc::fence_smem_to_async();
+      if (__syncthreads_or(!ok)) return;
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_addr(sa), b0 = tc::smem_addr(sbuf);
 #pragma unroll
-          for (int t = 0; t < EMU_S; ++t) Ad[(t * 32 + i) * EMU_KP + kk] = d[t];
-        }
+        for (int ks = 0; ks < TC_KS / 16; ++ks)
 #pragma unroll
-        for (int u = 0; u < NE; ++u) {
-          const int e = tid + u * NTHREADS;
-          int j, kk;
-          if (tb) { j = e & 31; kk = e >> 5; } else { kk = e & 31; j = e >> 5; }
-          uint16_t d[EMU_S];
-          emu_digits(vb[u], cexp[j], d);
+          for (int g = 0; g < G; ++g) {
+            const uint64_t ad = tc::smem_desc(a0 + g * (128 / 8) * TC_SBO + ks * 2 * TC_LBO, TC_LBO, TC_SBO);
+            const uint64_t bd = tc::smem_desc(b0 + ks * 2 * TC_LBO, TC_LBO, TC_SBO);
+            tc::mma_bf16(ts.tmem + 32 * g, ad, bd, tc::idesc_bf16_f32(128, 32 * (S - g)),
+                         (kacc == 0 && ks == 0 && g == 0) ? 0u : 1u);
+          }
+        tc::commit(buf ? mb1 : mb0);
+        ts.ncommit[buf] += 1;
+      }
+      ++nstage;
+      kacc += TC_KS;
+      const bool last = (s == tk.nseg - 1) && (k0 + TC_KS >= gs.k);
+      if (!last && kacc + TC_KS <= KMAX) continue;
+      // ---- drain: every MMA done, cells -> exact sums -> FP64
+      __syncthreads();  // ncommit of the last stage visible
+      const bool done = (ts.ncommit[0] == 0 || tc_wait(p, mb0, (ts.ncommit[0] - 1) & 1)) &&
+                        (ts.ncommit[1] == 0 || tc_wait(p, mb1, (ts.ncommit[1] - 1) & 1));
+      if (__syncthreads_or(!done)) return;
+      tc::fence_after_sync();
+      kacc = 0;
+      long long* slice = reinterpret_cast<long long*>(stage);  // [4 p][32 i][4 j] x (hi, lo), aliases staging
+      float* slicef = reinterpret_cast<float*>(stage);          // [4 p][32 i][4 j] (S = 4)
+      const uint32_t trow = ts.tmem + ((uint32_t)(32 * warp) << 16);
+      // column slices of 4: lane block p (= warp) reads its S - G p column blocks
+#pragma unroll 1
+      for (int js = 0; js < 8; ++js) {
+        uint32_t cell[S][4];  // every column block is read; blocks of levels >= S are not used
+        tc::ld_cells(trow + 4 * js, cell);
+        if constexpr (S == 8) {
+          long long hi[4], lo[4];
 #pragma unroll
-          for (int t = 0; t < EMU_S; ++t) Bd[(t * 32 + j) * EMU_KP + kk] = d[t];
-        }
-        __syncthreads();
+          for (int x = 0; x < 4; ++x) hi[x] = lo[x] = 0;
 #pragma unroll
-        for (int L = 0; L < EMU_S; ++L) {
-          float f[2][4] = {};
+          for (int c = 0; c < S; ++c) {
+            const int L = G * warp + c;
+            if (L <= S - 1) {
 #pragma unroll
-          for (int t = 0; t <= L; ++t) {
-            const int u = L - t;
-#pragma unroll
-            for (int ks = 0; ks < KC; ks += 16) {
-              const uint16_t* ap = Ad + (t * 32 + 16 * wr + g) * EMU_KP + ks + 2 * tq;
-              uint32_t a[4];
-              a[0] = *reinterpret_cast<const uint32_t*>(ap);
-              a[1] = *reinterpret_cast<const uint32_t*>(ap + 8 * EMU_KP);
-              a[2] = *reinterpret_cast<const uint32_t*>(ap + 8);
-              a[3] = *reinterpret_cast<const uint32_t*>(ap + 8 * EMU_KP + 8);
-#pragma unroll
-              for (int j = 0; j < 2; ++j) {
-                const uint16_t* bp = Bd + (u * 32 + 16 * wc + 8 * j + g) * EMU_KP + ks + 2 * tq;
-                mma_bf16(f[j], a, *reinterpret_cast<const uint32_t*>(bp), *reinterpret_cast<const uint32_t*>(bp + 8));
+              for (int x = 0; x < 4; ++x) {
+                const long long v = (long long)__float2int_rn(__uint_as_float(cell[c][x]));
+                if (L <= 3) hi[x] += v << (7 * (3 - L));
+                else lo[x] += v << (7 * (7 - L));
               }
             }
           }
 #pragma unroll
-          for (int j = 0; j < 2; ++j)
+          for (int x = 0; x < 4; ++x) {
+            slice[((warp * 32 + lane) * 4 + x) * 2] = hi[x];
+            slice[((warp * 32 + lane) * 4 + x) * 2 + 1] = lo[x];
+          }
+        } else {
+          float v[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) lev[(L * 8 + j * 4 + q) * NTHREADS + tid] += __float2int_rn(f[j][q]);
+          for (int x = 0; x < 4; ++x) v[x] = 0.0f;
+#pragma unroll
+          for (int c = 0; c < S; ++c) {
+            const int L = G * warp + c;
+            if (L <= S - 1) {
+#pragma unroll
+              for (int x = 0; x < 4; ++x) v[x] = fmaf(__uint_as_float(cell[c][x]), (float)(1 << (7 * (3 - L))), v[x]);
+            }
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x) slicef[(warp * 32 + lane) * 4 + x] = v[x];
+        }
+        __syncthreads();
+        // thread (warp, lane): output (row lane, column 4 js + warp)
+        {
+          const int j = 4 * js + warp;
+          double V;
+          if constexpr (S == 8) {
+            long long H = 0, Lo = 0;
+#pragma unroll
+            for (int pb = 0; pb < 4; ++pb) {
+              H += slice[((pb * 32 + lane) * 4 + warp) * 2];
+              Lo += slice[((pb * 32 + lane) * 4 + warp) * 2 + 1];
+            }
+            V = fma((double)H, 268435456.0, (double)Lo);  // H 2^28 + Lo, one rounding
+          } else {
+            float f = 0.0f;
+#pragma unroll
+            for (int pb = 0; pb < 4; ++pb) f += slicef[(pb * 32 + lane) * 4 + warp];
+            V = (double)f;
+          }
+          const int er = rexp[lane], ec = cexp[j];
+          const int k2 = max(er, 1) + max(ec, 1) - kScale;
+          const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
+          double& r = R[lane * 33 + j];
+          r = (er == 0x7ff || ec == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll) : fma(V, sc, r);
         }
         __syncthreads();
       }
-      // recombine exactly in 128-bit integers: V = sum_L lev_L 2^(8 (EMU_S - 1 - L)),
-      // then one rounding to FP64 and the scale 2^(E_i + F_j - kEmuScale + 8 (EMU_S - 1))
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          __int128 V = 0;
-#pragma unroll
-          for (int L = 0; L < EMU_S; ++L)
-            V += (__int128)lev[(L * 8 + j * 4 + q) * NTHREADS + tid] * ((__int128)1 << (8 * (EMU_S - 1 - L)));
-          const long long vh = (long long)(V >> 64);
-          const unsigned long long vl = (unsigned long long)V;
-          const double v = fma((double)vh, 18446744073709551616.0, (double)vl);
-          const int row = 16 * wr + g + 8 * (q >> 1), col = 16 * wc + 8 * j + 2 * tq + (q & 1);
-          const int k2 = rexp[row] + cexp[col] - kEmuScale + 8 * (EMU_S - 1);
-          // 2^k2 built from its exponent bits when it is a normal double
-          const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
-          // a row or column holding an Inf or NaN (biased exponent 0x7ff, the
-          // largest there is) has no digits: its products are NaN, as in FP64
-          res[j][q] = (rexp[row] == 0x7ff || cexp[col] == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                                : fma(v, sc, res[j][q]);
-        }
+      tc::fence_before_sync();
+      __syncthreads();  // TMEM reads done before the next MMAs; staging free again
     }
-    __syncthreads();
   }
-  // scatter to the accumulate<2,4> mapping: rows tx + 16 i, columns ty + 8 jj
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int row = 16 * wr + g + 8 * (q >> 1), col = 16 * wc + 8 * j + 2 * tq + (q & 1);
-      R[row * 33 + col] = res[j][q];
-    }
+  // to the accumulate<2,4> mapping
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
 #pragma unroll
@@ -1093,7 +1136,7 @@ __device__ int potrf_smem(double* X, int n) {
 }
 
 template <int TM, int TN>
-__device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double* smem) {
+__device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double* smem, TcShared& ts) {
   double* As = smem;             // KC x LDS
   double* Bs = smem + KC * LDS;  // KC x LDS
   double* T = smem;              // FB x LDS, reuses As/Bs after the K-loop
@@ -1102,12 +1145,11 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
   const int m = tk.m, n = tk.n;
   double acc[TM][TN];
   if (tk.op != OP_TRTRI) {
-    if (tk.prec == PREC_EMU64) {
-      if constexpr (TM == 2 && TN == 4) accumulate_emu(p, tk, sb, acc, smem);
-    } else if (tk.prec == PREC_FP32X) {
-      accumulate_f32<TM, TN>(p, tk, sb, acc, smem);
-    } else {
+    if (tk.prec == PREC_FP64) {
       accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
+    } else if constexpr (TM == 2 && TN == 4) {  // reduced-precision parts are <= 32 x 32 sub-tiles
+      if (tk.prec == PREC_EMU64) accumulate_tc<8>(p, tk, sb, acc, smem, ts);
+      else accumulate_tc<4>(p, tk, sb, acc, smem, ts);
     }
   }
 
@@ -1293,7 +1335,7 @@ __device__ bool task_part_ok(const KParams& p, const Task& tk, const Sub& sb) {
 }
 #endif
 
-__device__ void run_task(const KParams& p, const Task& tk, int t, int q, double* smem) {
+__device__ void run_task(const KParams& p, const Task& tk, int t, int q, double* smem, TcShared& ts) {
   if (tk.op == OP_PREP) {
     run_prep(p, tk, t);
     return;
@@ -1307,12 +1349,12 @@ __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double*
   }
 #endif
   switch (tk.pmode) {
-    case PM_ROWS2: run_sub<2, 8>(p, tk, sb, smem); break;
-    case PM_ROWS4: run_sub<1, 8>(p, tk, sb, smem); break;
+    case PM_ROWS2: run_sub<2, 8>(p, tk, sb, smem, ts); break;
+    case PM_ROWS4: run_sub<1, 8>(p, tk, sb, smem, ts); break;
     case PM_QUAD4:
     case PM_TRI3:
-    case PM_TILE32: run_sub<2, 4>(p, tk, sb, smem); break;
-    default: run_sub<4, 8>(p, tk, sb, smem); break;
+    case PM_TILE32: run_sub<2, 4>(p, tk, sb, smem, ts); break;
+    default: run_sub<4, 8>(p, tk, sb, smem, ts); break;
   }
 }
 
@@ -1323,8 +1365,23 @@ __device__ __forceinline__ unsigned smid() {
 }
 
 __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(1024) double smem[];
   __shared__ int s_item, s_last;
+  __shared__ TcShared ts;
+  // plans with reduced-precision products hold TC_COLS TMEM columns and two
+  // completion barriers for the kernel's lifetime (two CTAs per SM: 512)
+  if (p.use_tc) {
+    if (threadIdx.x < 32) tc::tmem_alloc(&ts.tmem, TC_COLS);
+    if (threadIdx.x == 0) {
+      tc::mbar_init(tc::smem_addr(&ts.mbar[0]), 1);
+      tc::mbar_init(tc::smem_addr(&ts.mbar[1]), 1);
+      tc::fence_mbar_init();
+      ts.ncommit[0] = ts.ncommit[1] = 0;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
   // request server: idle workers give up this long after the kernel started
   const unsigned long long deadline = p.serve ? gtimer() + p.sv.deadline : 0ull;
   for (;;) {
@@ -1348,7 +1405,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
     if (p.trace && threadIdx.x == 0) t_ready = gtimer();
     __threadfence();
     const Task tk = load_task(p, t);
-    run_task(p, tk, t, q, smem);
+    run_task(p, tk, t, q, smem, ts);
     __threadfence();
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -1373,9 +1430,24 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
       }
     }
   }
+  if (p.use_tc) {  // every part waited for its MMAs before it returned
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc::fence_after_sync();
+      tc::tmem_dealloc(ts.tmem, TC_COLS);
+    }
+    if (threadIdx.x == 0) {
+      tc::mbar_inval(tc::smem_addr(&ts.mbar[0]));
+      tc::mbar_inval(tc::smem_addr(&ts.mbar[1]));
+    }
+  }
 }
 
-size_t kernel_smem_bytes() { return sizeof(double) * (size_t)(2 * KC * LDS + FB * LDS); }
+size_t kernel_smem_bytes() {
+  const size_t fp64 = sizeof(double) * (size_t)(2 * KC * LDS + FB * LDS);
+  return fp64 > (size_t)TC_SMEM_BYTES ? fp64 : (size_t)TC_SMEM_BYTES;
+}
 
 int kernel_threads() { return NTHREADS; }
 

@@ -338,6 +338,7 @@ extern "C" int stiles_server_start(stiles_server_t h, double window_s) {
   p.budget_ns = h->budget_ns;
   p.buf_len = h->data_doubles;
   p.serve = 1;
+  p.use_tc = h->prec != PREC_FP64;
   for (int r = 0; r < 3; ++r) {
     p.sv.ring[r].slots = h->ring_slots + (size_t)r * ring;
     p.sv.ring[r].ctr = h->ring_ctr + 32 * r;
