@@ -882,6 +882,7 @@ def run_ours(args, world, rank, local):
     # algorithmic bytes of one launch: read A, write L, read L back, write Sigma
     alg_bytes = 4 * 8 * st.doubles
     st.close()
+    h2d_bytes, d2h_bytes = int(A_host.numel() * 8), int(S_host.numel() * 8 + 8)
     del A_host, S_host
     dgemm = None
     if not args.no_dgemm:
@@ -903,9 +904,9 @@ def run_ours(args, world, rank, local):
         "matrices_per_s": whole_job_rate(world, args.steps, 1.0, t_max),
         "logdet": logdet,
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": int(A_host.numel() * 8),
+        "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d_bytes,
                 "step_wall_ms": None if args.no_e2e else [round(v, 1) for v in e2e_wall],
-                "d2h_bytes_per_step": int(S_host.numel() * 8 + 8)},
+                "d2h_bytes_per_step": d2h_bytes},
         "gpu_launches": args.steps * (2 if not args.no_e2e else 1),
         "variants": variants,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

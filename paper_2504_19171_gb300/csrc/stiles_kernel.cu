@@ -537,13 +537,14 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // task part (at most 32 x 32 outputs) every row i of op(A) gets the biased
 // exponent E_i of its largest entry over all the task's segments and every
 // column j of op(B) the exponent F_j. Each entry becomes a signed fixed-point
-// integer X relative to that exponent, |X| < 2^(7S-2) (the largest entry of
-// the row keeps its 53-bit significand when S = 8; the others are rounded to
-// the same unit), written as S balanced base-128 digits d_t in [-64, 63],
-// X = sum_t d_t 128^(S-1-t), which bf16 holds exactly. A digit product is an
-// integer of magnitude at most 2^12; products of levels L = t + u <= S - 1
-// are kept. S = 8 (56 bits) is the emulated-FP64 mode, S = 4 (28 bits) the
-// FP32-class mode.
+// integer X relative to that exponent, |X| < 2^(DB S - 2) (the largest entry
+// of the row keeps its 53-bit significand in the emulated-FP64 mode; the
+// others are rounded to the same unit), written as S balanced base-2^DB
+// digits d_t in [-2^(DB-1), 2^(DB-1)), X = sum_t d_t 2^(DB (S-1-t)), which
+// bf16 holds exactly. A digit product is an integer of magnitude at most
+// 2^(2 DB - 2); products of levels L = t + u <= S - 1 are kept. Emulated FP64
+// uses S = 8 digits of DB = 7 bits (56 bits), the FP32-class mode S = 4
+// digits of 8 bits (32 bits).
 //
 // Tensor-core layout. D has M = 128 rows, made from a 32-row part by
 // stacking four digit planes of A: stack g (g < G = S / 4) holds plane
@@ -552,12 +553,13 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // the first 32 (S - g) columns of that concatenation into TMEM columns from
 // 32 g on, so TMEM cell (lane block p, column block c) collects the plane
 // pairs (g + G p, c - g), all of one level L = G p + c. A cell receives at
-// most G pairs per K step: its FP32 sums are integers below 2^24, hence
-// exact, for up to 2^24 / (G 2^12) = 4096 / G of K (2048 for S = 8). Before
-// that much K has been accumulated (or at the end of the task) the cells of
-// levels <= S - 1 are read -- warp p reads lane block p -- and combined per
-// output: exactly in two 64-bit halves for S = 8, in FP32 for S = 4. The
-// result, scaled by 2^(E_i + F_j - bias), is added to the part's FP64 value.
+// most G pairs per K step: in the emulated-FP64 mode its FP32 sums are
+// integers below 2^24, hence exact, for up to 2^24 / (G 2^12) = 2048 of K.
+// Before that much K has been accumulated (or at the end of the task) the
+// cells of levels <= S - 1 are read -- warp p reads lane block p -- and
+// combined per output: exactly in two 64-bit halves for emulated FP64, in
+// FP32 for the FP32-class mode. The result, scaled by 2^(E_i + F_j - bias),
+// is added to the part's FP64 value.
 // Non-finite operands (biased exponent 0x7ff) make their row or column NaN.
 
 constexpr int TC_KS = 32;           // K per staging buffer (two MMA K steps)
@@ -624,21 +626,29 @@ __device__ __forceinline__ long long fixed_point(double v, int emax) {
   return (bits >> 63) ? -X : X;
 }
 
-// The S digits of a pair of K-adjacent values (v0 at k, v1 at k + 1) as
-// packed bf16 pairs: w[t] = bf16(d_t(v0)) | bf16(d_t(v1)) << 16.
-template <int S>
+// C = sum_{t < S} 2^(DB-1) 2^(DB t): X + C has base-2^DB digits d_t + 2^(DB-1).
+template <int S, int DB>
+__host__ __device__ constexpr unsigned long long digit_bias() {
+  unsigned long long c = 0;
+  for (int t = 0; t < S; ++t) c |= 1ull << (DB * t + DB - 1);
+  return c;
+}
+
+// The S digits (DB bits each, balanced) of a pair of K-adjacent values (v0
+// at k, v1 at k + 1) as packed bf16 pairs: w[t] = bf16(d_t(v0)) | bf16(d_t(v1)) << 16.
+template <int S, int DB>
 __device__ __forceinline__ void digit_pairs(double v0, double v1, int emax, uint32_t (&w)[S]) {
-  constexpr int BITS = 7 * S - 2;
-  // C = sum_t 64 128^t: X + C has base-128 digits d_t + 64 in [0, 127]
-  constexpr unsigned long long C = 0x0081020408102040ull >> (7 * (8 - S));
+  constexpr int BITS = DB * S - 2;
+  constexpr unsigned long long C = digit_bias<S, DB>();
+  constexpr float kMagic = 8388608.0f + (float)(1 << (DB - 1));  // 2^23 + 2^(DB-1)
   const unsigned long long y0 = (unsigned long long)(fixed_point<BITS>(v0, emax) + (long long)C);
   const unsigned long long y1 = (unsigned long long)(fixed_point<BITS>(v1, emax) + (long long)C);
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    const int s = 7 * (S - 1 - t);
-    // exact float of (field - 64): 2^23 + field, minus 2^23 + 64; its bf16 is its upper half
-    const float f0 = __uint_as_float(0x4B000000u | (unsigned)((y0 >> s) & 0x7f)) - 8388672.0f;
-    const float f1 = __uint_as_float(0x4B000000u | (unsigned)((y1 >> s) & 0x7f)) - 8388672.0f;
+    const int s = DB * (S - 1 - t);
+    // exact float of (field - 2^(DB-1)): 2^23 + field, minus 2^23 + 2^(DB-1); its bf16 is its upper half
+    const float f0 = __uint_as_float(0x4B000000u | (unsigned)((y0 >> s) & ((1u << DB) - 1))) - kMagic;
+    const float f1 = __uint_as_float(0x4B000000u | (unsigned)((y1 >> s) & ((1u << DB) - 1))) - kMagic;
     w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
   }
 }
@@ -683,18 +693,22 @@ __device__ bool tc_wait(const KParams& p, uint32_t mbar, uint32_t parity) {
 // acc (accumulate<2,4> thread mapping: rows tx + 16 i, columns ty + 8 jj) =
 // sum over the task's segments of op(A) op(B) for the sub-tile sb (<= 32 x
 // 32), through S-digit products on the tensor cores (see above).
-template <int S>
+template <int S, int DB>
 __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[2][4], double* smem,
                               TcShared& ts) {
   constexpr int G = S / 4;                 // stacks of four A planes
-  constexpr int BITS = 7 * S - 2;
-  constexpr int KMAX = 4096 / G;           // K accumulated exactly in a TMEM cell
+  constexpr int BITS = DB * S - 2;
+  // K accumulated in a TMEM cell before it is read: exactly (integers below
+  // 2^24, at most G products of 2^(2 DB - 2) per K step) for emulated FP64;
+  // the FP32-class mode only needs FP32 accumulation
+  constexpr int KMAX = S == 8 ? (1 << 24) / (G << (2 * DB - 2)) : 4096;
   constexpr int ROWS = 32 * S;             // rows of the A stacks and of the B concatenation
   constexpr uint32_t OPB = ROWS * TC_KS * 2;  // bytes of one operand in a stage
   // k2 = E_i + F_j - kScale: X_a X_b summed over the kept levels is
-  // 2^(7 (S - 1)) V with V = sum_L S_L 2^(7 (S - 1 - L))
-  constexpr int kScale = 2044 + 2 * BITS - 7 * (S - 1);
-  static_assert(S == 4 || S == 8, "digit counts of the two modes");
+  // 2^(DB (S - 1)) V with V = sum_L S_L 2^(DB (S - 1 - L))
+  constexpr int kScale = 2044 + 2 * BITS - DB * (S - 1);
+  static_assert((S == 8 && DB == 7) || (S == 4 && DB == 8), "digit formats of the two modes");
+  static_assert(S == 4 || KMAX >= TC_KS, "exact chunk");
   uint8_t* stage = reinterpret_cast<uint8_t*>(smem);
   int* rexp = reinterpret_cast<int*>(stage + TC_EXP_OFF);
   int* cexp = rexp + 32;
@@ -742,7 +756,7 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
           if (kk + 1 < kc) v1 = __ldcg(P + step);
         }
         uint32_t w[S];
-        digit_pairs<S>(v0, v1, rexp[i], w);
+        digit_pairs<S, DB>(v0, v1, rexp[i], w);
 #pragma unroll
         for (int t = 0; t < S; ++t)
           *reinterpret_cast<uint32_t*>(sa + tc_off(128 * (t % G) + 32 * (t / G) + i, kk)) = w[t];
@@ -760,7 +774,7 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
           if (kk + 1 < kc) v1 = __ldcg(P + step);
         }
         uint32_t w[S];
-        digit_pairs<S>(v0, v1, cexp[j], w);
+        digit_pairs<S, DB>(v0, v1, cexp[j], w);
 #pragma unroll
         for (int t = 0; t < S; ++t) *reinterpret_cast<uint32_t*>(sbuf + tc_off(32 * t + j, kk)) = w[t];
       }
@@ -830,7 +844,7 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
             const int L = G * warp + c;
             if (L <= S - 1) {
 #pragma unroll
-              for (int x = 0; x < 4; ++x) v[x] = fmaf(__uint_as_float(cell[c][x]), (float)(1 << (7 * (3 - L))), v[x]);
+              for (int x = 0; x < 4; ++x) v[x] = fmaf(__uint_as_float(cell[c][x]), (float)(1 << (DB * (3 - L))), v[x]);
             }
           }
 #pragma unroll
@@ -1148,8 +1162,8 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
     if (tk.prec == PREC_FP64) {
       accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
     } else if constexpr (TM == 2 && TN == 4) {  // reduced-precision parts are <= 32 x 32 sub-tiles
-      if (tk.prec == PREC_EMU64) accumulate_tc<8>(p, tk, sb, acc, smem, ts);
-      else accumulate_tc<4>(p, tk, sb, acc, smem, ts);
+      if (tk.prec == PREC_EMU64) accumulate_tc<8, 7>(p, tk, sb, acc, smem, ts);
+      else accumulate_tc<4, 8>(p, tk, sb, acc, smem, ts);
     }
   }
 
