@@ -284,6 +284,12 @@ int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size
  * table fails its consistency check. */
 int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[9]);
 
+/* Test hook: CTAs of the persistent kernel that can be resident on one SM of
+ * the current device with the shared memory of an FP64 plan (tensor_parts =
+ * 0) or of a plan with tensor-core parts (1); the kernel is designed for 2.
+ * Returns STILES_ERR_CUDA if the query fails. */
+int stiles_debug_occupancy(int tensor_parts, int *blocks_per_sm);
+
 /* Test hook: build the plan `which` (as in stiles_plan_stats) for a shape and
  * emulate one launch of it on the host: every memory access of every task
  * part stays inside its buffer, every queue stays inside its capacity, and

@@ -447,6 +447,11 @@ extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, 
   return STILES_OK;
 }
 
+extern "C" int stiles_debug_occupancy(int tensor_parts, int* blocks_per_sm) {
+  if (!blocks_per_sm) return STILES_ERR_INVALID_ARG;
+  return kernel_occupancy(tensor_parts != 0, blocks_per_sm) == cudaSuccess ? STILES_OK : STILES_ERR_CUDA;
+}
+
 extern "C" int stiles_debug_validate(int nt, int b, int band, int arrow, int which) {
   const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
   if (kind < 0 || kind > 2 || prec > PREC_FP32X || !tune_valid(tune) || nt < 1 || b < 1 || band < 0 || arrow < 0)
@@ -741,10 +746,10 @@ static int build_batch_graph(stiles_batch* h, const double* A, double* L, double
   if (h->dev.ntasks > 0) {
     void* args[1] = {&h->kp};
     cudaKernelNodeParams kn{};
-    kn.func = const_cast<void*>(persistent_kernel_ptr());
+    kn.func = const_cast<void*>(persistent_kernel_ptr(h->kp.use_tc != 0));
     kn.gridDim = dim3((unsigned)h->grid);
     kn.blockDim = dim3((unsigned)kernel_threads());
-    kn.sharedMemBytes = (unsigned)kernel_smem_bytes();
+    kn.sharedMemBytes = (unsigned)kernel_smem_bytes(h->kp.use_tc != 0);
     kn.kernelParams = args;
     ok = ok && cudaGraphAddKernelNode(&n, g, deps.data(), deps.size(), &kn) == cudaSuccess;
   }

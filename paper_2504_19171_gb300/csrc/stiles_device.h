@@ -129,11 +129,13 @@ struct KParams {
   ServeDev sv;
 };
 
-size_t kernel_smem_bytes();
+size_t kernel_smem_bytes(bool use_tc);  // dynamic shared memory of a launch
 int kernel_threads();
 // Sets the kernel's dynamic shared-memory limit on the current device (once per device).
 cudaError_t configure_persistent();
-const void* persistent_kernel_ptr();
+const void* persistent_kernel_ptr(bool use_tc);  // the kernel instance a plan launches
 cudaError_t launch_persistent(const KParams& p, int grid, cudaStream_t stream);
+// Resident CTAs of the persistent kernel per SM at the launch's shared memory.
+cudaError_t kernel_occupancy(bool use_tc, int* blocks_per_sm);
 
 }  // namespace stiles

@@ -563,7 +563,7 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // Non-finite operands (biased exponent 0x7ff) make their row or column NaN.
 
 constexpr int TC_KS = 32;           // K per staging buffer (two MMA K steps)
-constexpr int TC_COLS = 256;        // TMEM columns per CTA (two CTAs per SM share 512)
+constexpr uint32_t TC_COLS = 256;   // TMEM columns per CTA (two CTAs per SM share 512)
 constexpr int TC_STAGE_BYTES_MAX = 2 * 32 * 8 * TC_KS * 2;  // A and B digit planes of S = 8
 // shared memory of a tensor part: two staging buffers, the row / column
 // exponents, then the part's FP64 result (32 x 33 doubles)
@@ -1149,8 +1149,8 @@ __device__ int potrf_smem(double* X, int n) {
   return s_bad < n ? s_bad : -1;
 }
 
-template <int TM, int TN>
-__device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double* smem, TcShared& ts) {
+template <bool TC, int TM, int TN>
+__device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double* smem, TcShared* ts) {
   double* As = smem;             // KC x LDS
   double* Bs = smem + KC * LDS;  // KC x LDS
   double* T = smem;              // FB x LDS, reuses As/Bs after the K-loop
@@ -1159,11 +1159,12 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
   const int m = tk.m, n = tk.n;
   double acc[TM][TN];
   if (tk.op != OP_TRTRI) {
-    if (tk.prec == PREC_FP64) {
+    if constexpr (TC && TM == 2 && TN == 4) {  // reduced-precision parts are <= 32 x 32 sub-tiles
+      if (tk.prec == PREC_EMU64) accumulate_tc<8, 7>(p, tk, sb, acc, smem, *ts);
+      else if (tk.prec == PREC_FP32X) accumulate_tc<4, 8>(p, tk, sb, acc, smem, *ts);
+      else accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
+    } else {
       accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
-    } else if constexpr (TM == 2 && TN == 4) {  // reduced-precision parts are <= 32 x 32 sub-tiles
-      if (tk.prec == PREC_EMU64) accumulate_tc<8, 7>(p, tk, sb, acc, smem, ts);
-      else accumulate_tc<4, 8>(p, tk, sb, acc, smem, ts);
     }
   }
 
@@ -1349,7 +1350,8 @@ __device__ bool task_part_ok(const KParams& p, const Task& tk, const Sub& sb) {
 }
 #endif
 
-__device__ void run_task(const KParams& p, const Task& tk, int t, int q, double* smem, TcShared& ts) {
+template <bool TC>
+__device__ void run_task(const KParams& p, const Task& tk, int t, int q, double* smem, TcShared* ts) {
   if (tk.op == OP_PREP) {
     run_prep(p, tk, t);
     return;
@@ -1363,12 +1365,12 @@ __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double*
   }
 #endif
   switch (tk.pmode) {
-    case PM_ROWS2: run_sub<2, 8>(p, tk, sb, smem, ts); break;
-    case PM_ROWS4: run_sub<1, 8>(p, tk, sb, smem, ts); break;
+    case PM_ROWS2: run_sub<TC, 2, 8>(p, tk, sb, smem, ts); break;
+    case PM_ROWS4: run_sub<TC, 1, 8>(p, tk, sb, smem, ts); break;
     case PM_QUAD4:
     case PM_TRI3:
-    case PM_TILE32: run_sub<2, 4>(p, tk, sb, smem, ts); break;
-    default: run_sub<4, 8>(p, tk, sb, smem, ts); break;
+    case PM_TILE32: run_sub<TC, 2, 4>(p, tk, sb, smem, ts); break;
+    default: run_sub<TC, 4, 8>(p, tk, sb, smem, ts); break;
   }
 }
 
@@ -1378,19 +1380,34 @@ __device__ __forceinline__ unsigned smid() {
   return r;
 }
 
+// Per-CTA state of the tensor path, in static shared memory of the kernel
+// instance that has one.
+template <bool TC>
+__device__ __forceinline__ TcShared* tc_shared() {
+  if constexpr (TC) {
+    __shared__ TcShared ts;
+    return &ts;
+  } else {
+    return nullptr;
+  }
+}
+
+// Two instances: TC = false for plans whose products are all FP64 (no
+// tensor-core code at all), TC = true for plans with reduced-precision parts.
+template <bool TC>
 __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
-  extern __shared__ __align__(1024) double smem[];
+  extern __shared__ __align__(16) double smem[];
   __shared__ int s_item, s_last;
-  __shared__ TcShared ts;
+  TcShared* ts = tc_shared<TC>();
   // plans with reduced-precision products hold TC_COLS TMEM columns and two
   // completion barriers for the kernel's lifetime (two CTAs per SM: 512)
-  if (p.use_tc) {
-    if (threadIdx.x < 32) tc::tmem_alloc(&ts.tmem, TC_COLS);
+  if constexpr (TC) {
+    if (threadIdx.x < 32) tc::tmem_alloc<TC_COLS>(&ts->tmem);
     if (threadIdx.x == 0) {
-      tc::mbar_init(tc::smem_addr(&ts.mbar[0]), 1);
-      tc::mbar_init(tc::smem_addr(&ts.mbar[1]), 1);
+      tc::mbar_init(tc::smem_addr(&ts->mbar[0]), 1);
+      tc::mbar_init(tc::smem_addr(&ts->mbar[1]), 1);
       tc::fence_mbar_init();
-      ts.ncommit[0] = ts.ncommit[1] = 0;
+      ts->ncommit[0] = ts->ncommit[1] = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -1419,7 +1436,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
     if (p.trace && threadIdx.x == 0) t_ready = gtimer();
     __threadfence();
     const Task tk = load_task(p, t);
-    run_task(p, tk, t, q, smem, ts);
+    run_task<TC>(p, tk, t, q, smem, ts);
     __threadfence();
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -1444,31 +1461,35 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_kernel(KParams p) {
       }
     }
   }
-  if (p.use_tc) {  // every part waited for its MMAs before it returned
+  if constexpr (TC) {  // every part waited for its MMAs before it returned
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x < 32) {
       tc::fence_after_sync();
-      tc::tmem_dealloc(ts.tmem, TC_COLS);
+      tc::tmem_dealloc<TC_COLS>(ts->tmem);
     }
     if (threadIdx.x == 0) {
-      tc::mbar_inval(tc::smem_addr(&ts.mbar[0]));
-      tc::mbar_inval(tc::smem_addr(&ts.mbar[1]));
+      tc::mbar_inval(tc::smem_addr(&ts->mbar[0]));
+      tc::mbar_inval(tc::smem_addr(&ts->mbar[1]));
     }
   }
 }
 
-size_t kernel_smem_bytes() {
+// Dynamic shared memory of a launch: the FP64 tasks' staging and block
+// regions, or more when the plan has tensor-core parts.
+size_t kernel_smem_bytes(bool use_tc) {
   const size_t fp64 = sizeof(double) * (size_t)(2 * KC * LDS + FB * LDS);
-  return fp64 > (size_t)TC_SMEM_BYTES ? fp64 : (size_t)TC_SMEM_BYTES;
+  return use_tc && (size_t)TC_SMEM_BYTES > fp64 ? (size_t)TC_SMEM_BYTES : fp64;
 }
 
 int kernel_threads() { return NTHREADS; }
 
-const void* persistent_kernel_ptr() { return (const void*)persistent_kernel; }
+const void* persistent_kernel_ptr(bool use_tc) {
+  return use_tc ? (const void*)persistent_kernel<true> : (const void*)persistent_kernel<false>;
+}
 
-// The shared-memory limit is a per-device attribute of the kernel: it is set
-// once for every device the process launches on (the current one here).
+// The shared-memory limit is a per-device attribute of each kernel instance:
+// it is set once for every device the process launches on (the current one).
 cudaError_t configure_persistent() {
   constexpr int kMaxDevices = 64;
   static std::atomic<bool> configured[kMaxDevices];
@@ -1476,21 +1497,35 @@ cudaError_t configure_persistent() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices)
-    return cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kernel_smem_bytes());
-  if (configured[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  const bool cached = dev >= 0 && dev < kMaxDevices;
+  if (cached && configured[dev].load(std::memory_order_acquire)) return cudaSuccess;
   std::lock_guard<std::mutex> lock(mu);
-  if (configured[dev].load(std::memory_order_relaxed)) return cudaSuccess;
-  e = cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kernel_smem_bytes());
-  if (e == cudaSuccess) configured[dev].store(true, std::memory_order_release);
+  if (cached && configured[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = cudaFuncSetAttribute(persistent_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kernel_smem_bytes(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(persistent_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kernel_smem_bytes(true));
+  if (e == cudaSuccess && cached) configured[dev].store(true, std::memory_order_release);
   return e;
+}
+
+cudaError_t kernel_occupancy(bool use_tc, int* blocks_per_sm) {
+  cudaError_t e = configure_persistent();
+  if (e != cudaSuccess) return e;
+  return use_tc ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel<true>, NTHREADS,
+                                                                kernel_smem_bytes(true))
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel<false>, NTHREADS,
+                                                                kernel_smem_bytes(false));
 }
 
 cudaError_t launch_persistent(const KParams& p, int grid, cudaStream_t stream) {
   cudaError_t e = configure_persistent();
   if (e != cudaSuccess) return e;
-  persistent_kernel<<<grid, NTHREADS, kernel_smem_bytes(), stream>>>(p);
+  if (p.use_tc)
+    persistent_kernel<true><<<grid, NTHREADS, kernel_smem_bytes(true), stream>>>(p);
+  else
+    persistent_kernel<false><<<grid, NTHREADS, kernel_smem_bytes(false), stream>>>(p);
   return cudaGetLastError();
 }
 

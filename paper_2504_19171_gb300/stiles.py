@@ -54,6 +54,7 @@ EXPORTS = [
     "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
     "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status", "stiles_server_submit_values",
+    "stiles_debug_occupancy",
 ]
 
 
@@ -84,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "stiles_debug_break_plan": [vp, i32],
         "stiles_destroy": [vp],
         "stiles_strerror": [i32],
+        "stiles_debug_occupancy": [ctypes.c_int, P(ctypes.c_int)],
         "stiles_trace": [vp, P(ctypes.c_ulonglong), sz, P(sz)],
         "stiles_factor_selinv_noalloc": [vp, vp, vp, vp, vp],
         "stiles_debug_validate": [i32, i32, i32, i32, i32],
@@ -227,6 +229,14 @@ def stiles_debug_check_corrupted(nt: int, b: int, band: int, arrow: int, which: 
 
 def stiles_debug_break_plan(h: int, which: int) -> None:
     _check(_lib.stiles_debug_break_plan(h, which), "stiles_debug_break_plan")
+
+
+def stiles_debug_occupancy(tensor_parts: bool) -> int:
+    """Resident CTAs of the persistent kernel per SM (FP64 plans, or plans
+    with tensor-core parts)."""
+    n = ctypes.c_int(0)
+    _check(_lib.stiles_debug_occupancy(1 if tensor_parts else 0, ctypes.byref(n)), "stiles_debug_occupancy")
+    return n.value
 
 
 def stiles_trace(h: int) -> np.ndarray:
