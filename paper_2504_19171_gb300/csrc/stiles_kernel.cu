@@ -585,25 +585,48 @@ __device__ __forceinline__ int biased_exp(double v) {
 // out[i] = max(out[i], largest biased exponent over k < K of element (i, k))
 // of a panel of n <= 32 vectors: element (i, k) sits at P[i + k ld] when
 // `along_i` (the vectors' index is the contiguous one), else at P[k + i ld].
-// Loads follow the contiguous dimension. Ends with a block barrier.
+// Loads follow the contiguous dimension, 16 independent ones in flight per
+// thread. Ends with a block barrier.
 __device__ __forceinline__ void max_exp_into(const double* P, int ld, bool along_i, int n, int K, int* out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (along_i) {  // lanes over i, warps over k
+  constexpr int U = 16;
+  if (along_i) {  // lanes over i, warps over k (k = warp + 4 u)
     int mx = 0;
     if (lane < n)
-      for (int k = warp; k < K; k += 4) mx = max(mx, biased_exp(__ldcg(P + lane + (int64_t)k * ld)));
+      for (int k0 = warp; k0 < K; k0 += 4 * U) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = k0 + 4 * u < K ? __ldcg(P + lane + (int64_t)(k0 + 4 * u) * ld) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) mx = max(mx, biased_exp(v[u]));
+      }
     __shared__ int part[4][32];
     part[warp][lane] = mx;
     __syncthreads();
     if (warp == 0) out[lane] = max(out[lane], max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane])));
-  } else {  // one warp per vector, lanes over k
-    for (int i = warp; i < 32; i += 4) {
-      int mx = 0;
-      if (i < n)
-        for (int k = lane; k < K; k += 32) mx = max(mx, biased_exp(__ldcg(P + k + (int64_t)i * ld)));
+  } else {  // lanes over k; warp w takes vectors w, w + 4, ..., w + 28 at once (two k per lane)
+    int mx[8];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) out[i] = max(out[i], mx);
+    for (int v = 0; v < 8; ++v) mx[v] = 0;
+    for (int k0 = lane; k0 < K; k0 += 64) {
+      double x[8][2];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const int i = warp + 4 * v;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = k0 + 32 * h;
+          x[v][h] = (i < n && k < K) ? __ldcg(P + k + (int64_t)i * ld) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 8; ++v) mx[v] = max(mx[v], max(biased_exp(x[v][0]), biased_exp(x[v][1])));
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx[v] = max(mx[v], __shfl_xor_sync(0xffffffffu, mx[v], o));
+      if (lane == 0) out[warp + 4 * v] = max(out[warp + 4 * v], mx[v]);
     }
   }
   __syncthreads();
@@ -664,17 +687,15 @@ constexpr uint32_t TC_SBO = (TC_KS / 8) * 128;   // 8-row groups
 
 // Panel element owned by slot q (0..3) of this thread, for a stage of 32
 // vectors x TC_KS: vector index `vi` and the even K offset `kk` of its pair.
-// When the vectors are the contiguous dimension, lanes run over vectors;
-// otherwise over K pairs.
-__device__ __forceinline__ void tc_slot(bool along_vec, int q, int& vi, int& kk) {
-  const int tid = threadIdx.x;
-  if (along_vec) {
-    vi = tid & 31;
-    kk = 2 * ((tid >> 5) + 4 * q);
-  } else {
-    kk = 2 * (tid & 15);
-    vi = (tid >> 4) + 8 * q;
-  }
+// Warp w takes the 8-vector group w, slot q the K core matrix q, and lane
+// (r, kp) = (lane % 8, lane / 8) the vector 8 w + r and K pair kp of it: the
+// warp's 32 packed-pair stores then fill the 32 words of one core matrix
+// (no shared-memory bank conflict), and its loads read 8 x 64 contiguous
+// bytes whichever dimension of the operand is the contiguous one.
+__device__ __forceinline__ void tc_slot(int q, int& vi, int& kk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  vi = 8 * warp + (lane & 7);
+  kk = 8 * q + 2 * (lane >> 3);
 }
 
 // Bounded wait for phase `parity` of a staging barrier (all threads).
@@ -690,9 +711,37 @@ __device__ bool tc_wait(const KParams& p, uint32_t mbar, uint32_t parity) {
   return true;
 }
 
+// Raw values of one stage (TC_KS of K from k0) of the part's operands, as
+// this thread's four K-adjacent pairs of op(A) and of op(B) (zero outside
+// the part or the segment).
+__device__ __forceinline__ void tc_load(const double* A, const double* B, const Seg& gs, const Sub& sb, int k0,
+                                        double (&va)[8], double (&vb)[8]) {
+  const bool ta = gs.trans & 1, tb = gs.trans & 2;
+  const int kc = min(TC_KS, gs.k - k0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int i, kk;
+    tc_slot(q, i, kk);
+    const double* P = ta ? A + (int64_t)(k0 + kk) + (int64_t)i * gs.lda : A + (int64_t)i + (int64_t)(k0 + kk) * gs.lda;
+    const int64_t step = ta ? 1 : gs.lda;
+    va[2 * q] = (i < sb.rm && kk < kc) ? __ldcg(P) : 0.0;
+    va[2 * q + 1] = (i < sb.rm && kk + 1 < kc) ? __ldcg(P + step) : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int j, kk;
+    tc_slot(q, j, kk);
+    const double* P = tb ? B + (int64_t)j + (int64_t)(k0 + kk) * gs.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * gs.ldb;
+    const int64_t step = tb ? gs.ldb : 1;
+    vb[2 * q] = (j < sb.cn && kk < kc) ? __ldcg(P) : 0.0;
+    vb[2 * q + 1] = (j < sb.cn && kk + 1 < kc) ? __ldcg(P + step) : 0.0;
+  }
+}
+
 // acc (accumulate<2,4> thread mapping: rows tx + 16 i, columns ty + 8 jj) =
 // sum over the task's segments of op(A) op(B) for the sub-tile sb (<= 32 x
-// 32), through S-digit products on the tensor cores (see above).
+// 32), through S-digit products on the tensor cores (see above). The next
+// stage's operands are loaded while the current one is split into digits.
 template <int S, int DB>
 __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[2][4], double* smem,
                               TcShared& ts) {
@@ -709,6 +758,7 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
   constexpr int kScale = 2044 + 2 * BITS - DB * (S - 1);
   static_assert((S == 8 && DB == 7) || (S == 4 && DB == 8), "digit formats of the two modes");
   static_assert(S == 4 || KMAX >= TC_KS, "exact chunk");
+  static_assert(32 * 4 * 32 * 16 <= 2 * TC_STAGE_BYTES_MAX, "drain buffer fits the staging region");
   uint8_t* stage = reinterpret_cast<uint8_t*>(smem);
   int* rexp = reinterpret_cast<int*>(stage + TC_EXP_OFF);
   int* cexp = rexp + 32;
@@ -735,48 +785,44 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
     const bool ta = gs.trans & 1, tb = gs.trans & 2;
     const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
     const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
+    double na[8], nb[8];  // the next stage's values, in flight
+    tc_load(A, B, gs, sb, 0, na, nb);
     for (int k0 = 0; k0 < gs.k; k0 += TC_KS) {
-      const int kc = min(TC_KS, gs.k - k0);
+      double ca[8], cb[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        ca[x] = na[x];
+        cb[x] = nb[x];
+      }
+      if (k0 + TC_KS < gs.k) tc_load(A, B, gs, sb, k0 + TC_KS, na, nb);
       const int buf = nstage & 1;
       uint8_t* sa = stage + buf * TC_STAGE_BYTES_MAX;
       uint8_t* sbuf = sa + OPB;
       // the MMAs that last read this buffer (two stages ago) must be done
       // (a wait that runs out of budget ends the part on every thread at the barrier below)
       const bool ok = nstage < 2 || tc_wait(p, buf ? mb1 : mb0, (ts.ncommit[buf] - 1) & 1);
-      // op(A) rows: digit t of row i goes to stack row 128 (t % G) + 32 (t / G) + i
+      if (ok) {
+        // op(A) rows: digit t of row i goes to stack row 128 (t % G) + 32 (t / G) + i
 #pragma unroll
-      for (int q = 0; q < 4 && ok; ++q) {
-        int i, kk;
-        tc_slot(!ta, q, i, kk);
-        double v0 = 0.0, v1 = 0.0;
-        if (i < sb.rm) {
-          const double* P = ta ? A + (int64_t)(k0 + kk) + (int64_t)i * gs.lda : A + (int64_t)i + (int64_t)(k0 + kk) * gs.lda;
-          const int64_t step = ta ? 1 : gs.lda;
-          if (kk < kc) v0 = __ldcg(P);
-          if (kk + 1 < kc) v1 = __ldcg(P + step);
+        for (int q = 0; q < 4; ++q) {
+          int i, kk;
+          tc_slot(q, i, kk);
+          uint32_t w[S];
+          digit_pairs<S, DB>(ca[2 * q], ca[2 * q + 1], rexp[i], w);
+#pragma unroll
+          for (int t = 0; t < S; ++t)
+            *reinterpret_cast<uint32_t*>(sa + tc_off(128 * (t % G) + 32 * (t / G) + i, kk)) = w[t];
         }
-        uint32_t w[S];
-        digit_pairs<S, DB>(v0, v1, rexp[i], w);
+        // op(B) columns: digit u of column j goes to row 32 u + j
 #pragma unroll
-        for (int t = 0; t < S; ++t)
-          *reinterpret_cast<uint32_t*>(sa + tc_off(128 * (t % G) + 32 * (t / G) + i, kk)) = w[t];
-      }
-      // op(B) columns: digit u of column j goes to row 32 u + j
+        for (int q = 0; q < 4; ++q) {
+          int j, kk;
+          tc_slot(q, j, kk);
+          uint32_t w[S];
+          digit_pairs<S, DB>(cb[2 * q], cb[2 * q + 1], cexp[j], w);
 #pragma unroll
-      for (int q = 0; q < 4 && ok; ++q) {
-        int j, kk;
-        tc_slot(tb, q, j, kk);
-        double v0 = 0.0, v1 = 0.0;
-        if (j < sb.cn) {
-          const double* P = tb ? B + (int64_t)j + (int64_t)(k0 + kk) * gs.ldb : B + (int64_t)(k0 + kk) + (int64_t)j * gs.ldb;
-          const int64_t step = tb ? gs.ldb : 1;
-          if (kk < kc) v0 = __ldcg(P);
-          if (kk + 1 < kc) v1 = __ldcg(P + step);
+          for (int t = 0; t < S; ++t) *reinterpret_cast<uint32_t*>(sbuf + tc_off(32 * t + j, kk)) = w[t];
         }
-        uint32_t w[S];
-        digit_pairs<S, DB>(v0, v1, cexp[j], w);
-#pragma unroll
-        for (int t = 0; t < S; ++t) *reinterpret_cast<uint32_t*>(sbuf + tc_off(32 * t + j, kk)) = w[t];
       }
       tc::fence_smem_to_async();
       if (__syncthreads_or(!ok)) return;
@@ -806,10 +852,11 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
       if (__syncthreads_or(!done)) return;
       tc::fence_after_sync();
       kacc = 0;
-      long long* slice = reinterpret_cast<long long*>(stage);  // [4 p][32 i][4 j] x (hi, lo), aliases staging
-      float* slicef = reinterpret_cast<float*>(stage);          // [4 p][32 i][4 j] (S = 4)
+      // lane block p (= warp) reads its cells, four columns at a time, and
+      // leaves its partial sums for every (column, row) in the staging region
+      long long* part = reinterpret_cast<long long*>(stage);  // [32 j][4 p][32 i] x (hi, lo)
+      float* partf = reinterpret_cast<float*>(stage);          // [32 j][4 p][32 i]
       const uint32_t trow = ts.tmem + ((uint32_t)(32 * warp) << 16);
-      // column slices of 4: lane block p (= warp) reads its S - G p column blocks
 #pragma unroll 1
       for (int js = 0; js < 8; ++js) {
         uint32_t cell[S][4];  // every column block is read; blocks of levels >= S are not used
@@ -825,57 +872,56 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
 #pragma unroll
               for (int x = 0; x < 4; ++x) {
                 const long long v = (long long)__float2int_rn(__uint_as_float(cell[c][x]));
-                if (L <= 3) hi[x] += v << (7 * (3 - L));
-                else lo[x] += v << (7 * (7 - L));
+                if (L <= 3) hi[x] += v << (DB * (3 - L));
+                else lo[x] += v << (DB * (7 - L));
               }
             }
           }
 #pragma unroll
           for (int x = 0; x < 4; ++x) {
-            slice[((warp * 32 + lane) * 4 + x) * 2] = hi[x];
-            slice[((warp * 32 + lane) * 4 + x) * 2 + 1] = lo[x];
+            const int e = ((4 * js + x) * 4 + warp) * 32 + lane;
+            part[2 * e] = hi[x];
+            part[2 * e + 1] = lo[x];
           }
         } else {
-          float v[4];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) v[x] = 0.0f;
+          for (int x = 0; x < 4; ++x) {
+            float v = 0.0f;
 #pragma unroll
-          for (int c = 0; c < S; ++c) {
-            const int L = G * warp + c;
-            if (L <= S - 1) {
-#pragma unroll
-              for (int x = 0; x < 4; ++x) v[x] = fmaf(__uint_as_float(cell[c][x]), (float)(1 << (DB * (3 - L))), v[x]);
+            for (int c = 0; c < S; ++c) {
+              const int L = G * warp + c;
+              if (L <= S - 1) v = fmaf(__uint_as_float(cell[c][x]), (float)(1 << (DB * (3 - L))), v);
             }
+            partf[((4 * js + x) * 4 + warp) * 32 + lane] = v;
           }
-#pragma unroll
-          for (int x = 0; x < 4; ++x) slicef[(warp * 32 + lane) * 4 + x] = v[x];
         }
-        __syncthreads();
-        // thread (warp, lane): output (row lane, column 4 js + warp)
-        {
-          const int j = 4 * js + warp;
-          double V;
-          if constexpr (S == 8) {
-            long long H = 0, Lo = 0;
+      }
+      __syncthreads();
+      // thread (warp, lane): outputs (row lane, column 4 js + warp)
+#pragma unroll 2
+      for (int js = 0; js < 8; ++js) {
+        const int j = 4 * js + warp;
+        double V;
+        if constexpr (S == 8) {
+          long long H = 0, Lo = 0;
 #pragma unroll
-            for (int pb = 0; pb < 4; ++pb) {
-              H += slice[((pb * 32 + lane) * 4 + warp) * 2];
-              Lo += slice[((pb * 32 + lane) * 4 + warp) * 2 + 1];
-            }
-            V = fma((double)H, 268435456.0, (double)Lo);  // H 2^28 + Lo, one rounding
-          } else {
-            float f = 0.0f;
-#pragma unroll
-            for (int pb = 0; pb < 4; ++pb) f += slicef[(pb * 32 + lane) * 4 + warp];
-            V = (double)f;
+          for (int pb = 0; pb < 4; ++pb) {
+            const int e = (j * 4 + pb) * 32 + lane;
+            H += part[2 * e];
+            Lo += part[2 * e + 1];
           }
-          const int er = rexp[lane], ec = cexp[j];
-          const int k2 = max(er, 1) + max(ec, 1) - kScale;
-          const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
-          double& r = R[lane * 33 + j];
-          r = (er == 0x7ff || ec == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll) : fma(V, sc, r);
+          V = fma((double)H, (double)(1ll << (4 * DB)), (double)Lo);  // H 2^(4 DB) + Lo, one rounding
+        } else {
+          float f = 0.0f;
+#pragma unroll
+          for (int pb = 0; pb < 4; ++pb) f += partf[(j * 4 + pb) * 32 + lane];
+          V = (double)f;
         }
-        __syncthreads();
+        const int er = rexp[lane], ec = cexp[j];
+        const int k2 = max(er, 1) + max(ec, 1) - kScale;
+        const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
+        double& r = R[lane * 33 + j];
+        r = (er == 0x7ff || ec == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll) : fma(V, sc, r);
       }
       tc::fence_before_sync();
       __syncthreads();  // TMEM reads done before the next MMAs; staging free again
