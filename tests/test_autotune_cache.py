@@ -23,3 +23,24 @@ def test_candidates_are_valid_tuning_codes():
     from paper_2504_19171_gb300 import stiles as S
     for c in AT.CANDIDATES:
         assert S.stiles_debug_validate(5, 64, 1, 8, S.PLAN_FUSED + 256 * c) == S.STILES_OK
+
+
+def test_single_regime_has_its_own_key(tmp_path):
+    # a long matrix alone and a batch of short ones are tuned separately
+    assert AT.key_of(1024, 1, 64, 0, "single") != AT.key_of(1024, 1, 64, 0)
+    assert AT.key_of(1024, 1, 64, 0, "single").endswith(":single")
+    p = tmp_path / "t.json"
+    p.write_text(json.dumps({AT.key_of(1024, 1, 64, 1, "single"): {"code": 3, "grid_per_sm": 1, "seconds": {}},
+                             AT.key_of(1024, 1, 64, 1): {"code": 26, "seconds": {}}}))
+    t = AT.Autotuner(str(p))
+    assert t.best_single(1024, 1, 64, 1) == (3, 1)
+    assert t.best(1024, 1, 64, 1) == 26
+    assert t.cached(1024, 1, 64, 2) is None
+
+
+def test_shipped_cache_entries_are_valid():
+    from paper_2504_19171_gb300 import stiles as S
+    t = AT.Autotuner(AT.default_cache_path())
+    for k, e in t.cache.items():
+        assert S.stiles_debug_validate(4, 64, 1, 8, S.PLAN_FUSED + 256 * int(e["code"])) == S.STILES_OK, k
+        assert int(e.get("grid_per_sm", 2)) in AT.GRID_PER_SM, k
