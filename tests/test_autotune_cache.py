@@ -44,3 +44,11 @@ def test_shipped_cache_entries_are_valid():
     for k, e in t.cache.items():
         assert S.stiles_debug_validate(4, 64, 1, 8, S.PLAN_FUSED + 256 * int(e["code"])) == S.STILES_OK, k
         assert int(e.get("grid_per_sm", 2)) in AT.GRID_PER_SM, k
+
+
+def test_single_regime_keeps_defaults_within_margin():
+    # a probe win smaller than the margin does not replace the defaults
+    t = {(0, 2): 1.000, (4, 2): 0.998, (1, 1): 1.2}
+    assert AT.Autotuner.pick_single(t) == (0, 2)
+    t[(26, 2)] = 0.90
+    assert AT.Autotuner.pick_single(t) == (26, 2)
