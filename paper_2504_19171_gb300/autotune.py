@@ -17,8 +17,9 @@ regime the matrix runs in:
   persistent CTAs per SM (two, or one so that each worker has its SM's FP64
   pipe to itself).
 
-Each key keeps the fastest candidate on its probe. Results are cached in a
-JSON file, keyed ``b:w:arrow_blocks:precision`` (batch) or
+Each batch key keeps the fastest candidate on its probe; a single key keeps
+the defaults unless a candidate beats them by SINGLE_MARGIN. Results are
+cached in a JSON file, keyed ``b:w:arrow_blocks:precision`` (batch) or
 ``b:w:arrow_blocks:precision:single``.
 """
 from __future__ import annotations
