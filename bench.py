@@ -46,8 +46,8 @@ FP32_SIMT_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
 # (the digit-pair products of the split-precision scheme: with s digits per
 # operand the levels t + u <= s - 1 are kept, s (s + 1) / 2 products), and the
 # pipe that runs them.
-VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (mma.sync)", "digits": 7, "products": 28},
-                    "fp32x": {"pipe": "FP32 SIMT FMA", "digits": None, "products": 1}}
+VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (tcgen05)", "digits": 8, "products": 36},
+                    "fp32x": {"pipe": "bf16 tensor (tcgen05)", "digits": 4, "products": 10}}
 
 # DRAM traffic of the persistent kernel per launch, from ncu captures of the
 # nt = 8 and nt = 16 cases of the same matrix family (0.809 GB and 2.164 GB):
