@@ -585,11 +585,11 @@ __device__ __forceinline__ int biased_exp(double v) {
 // out[i] = max(out[i], largest biased exponent over k < K of element (i, k))
 // of a panel of n <= 32 vectors: element (i, k) sits at P[i + k ld] when
 // `along_i` (the vectors' index is the contiguous one), else at P[k + i ld].
-// Loads follow the contiguous dimension, 32 independent ones in flight per
+// Loads follow the contiguous dimension, 16 independent ones in flight per
 // thread. Ends with a block barrier.
 __device__ __forceinline__ void max_exp_into(const double* P, int ld, bool along_i, int n, int K, int* out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int U = 32;
+  constexpr int U = 16;
   if (along_i) {  // lanes over i, warps over k (k = warp + 4 u)
     int mx = 0;
     if (lane < n)
@@ -604,25 +604,23 @@ __device__ __forceinline__ void max_exp_into(const double* P, int ld, bool along
     part[warp][lane] = mx;
     __syncthreads();
     if (warp == 0) out[lane] = max(out[lane], max(max(part[0][lane], part[1][lane]), max(part[2][lane], part[3][lane])));
-  } else {  // lanes over k; warp w takes vectors w, w + 4, ..., w + 28 at once (four k per lane)
+  } else {  // lanes over k; warp w takes vectors w, w + 4, ..., w + 28 at once (two k per lane)
     int mx[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) mx[v] = 0;
-    for (int k0 = lane; k0 < K; k0 += 128) {
-      double x[8][4];
+    for (int k0 = lane; k0 < K; k0 += 64) {
+      double x[8][2];
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
         const int i = warp + 4 * v;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
+        for (int h = 0; h < 2; ++h) {
           const int k = k0 + 32 * h;
           x[v][h] = (i < n && k < K) ? __ldcg(P + k + (int64_t)i * ld) : 0.0;
         }
       }
 #pragma unroll
-      for (int v = 0; v < 8; ++v)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) mx[v] = max(mx[v], biased_exp(x[v][h]));
+      for (int v = 0; v < 8; ++v) mx[v] = max(mx[v], max(biased_exp(x[v][0]), biased_exp(x[v][1])));
     }
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
