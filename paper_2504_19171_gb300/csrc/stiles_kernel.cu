@@ -543,8 +543,9 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // digits d_t in [-2^(DB-1), 2^(DB-1)), X = sum_t d_t 2^(DB (S-1-t)), which
 // bf16 holds exactly. A digit product is an integer of magnitude at most
 // 2^(2 DB - 2); products of levels L = t + u <= S - 1 are kept. Emulated FP64
-// uses S = 8 digits of DB = 7 bits (56 bits), the FP32-class mode S = 4
-// digits of 8 bits (32 bits).
+// uses S = 8 digits of DB = 8 bits (|X| < 2^62: entries down to 2^-9 of their
+// row maximum keep all 53 bits, the dropped levels weigh below 2^-56 of the
+// leading product), the FP32-class mode S = 4 digits of 8 bits (32 bits).
 //
 // Tensor-core layout. D has M = 128 rows, made from a 32-row part by
 // stacking four digit planes of A: stack g (g < G = S / 4) holds plane
@@ -554,7 +555,8 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // 32 g on, so TMEM cell (lane block p, column block c) collects the plane
 // pairs (g + G p, c - g), all of one level L = G p + c. A cell receives at
 // most G pairs per K step: in the emulated-FP64 mode its FP32 sums are
-// integers below 2^24, hence exact, for up to 2^24 / (G 2^12) = 2048 of K.
+// integers of magnitude at most 2^24, hence exact, for up to
+// 2^24 / (G 2^14) = 512 of K.
 // Before that much K has been accumulated (or at the end of the task) the
 // cells of levels <= S - 1 are read -- warp p reads lane block p -- and
 // combined per output: exactly in two 64-bit halves for emulated FP64, in
@@ -664,8 +666,9 @@ __device__ __forceinline__ void digit_pairs(double v0, double v1, int emax, uint
   constexpr int BITS = DB * S - 2;
   constexpr unsigned long long C = digit_bias<S, DB>();
   constexpr float kMagic = 8388608.0f + (float)(1 << (DB - 1));  // 2^23 + 2^(DB-1)
-  const unsigned long long y0 = (unsigned long long)(fixed_point<BITS>(v0, emax) + (long long)C);
-  const unsigned long long y1 = (unsigned long long)(fixed_point<BITS>(v1, emax) + (long long)C);
+  // in unsigned arithmetic: with DB S = 64 the bias C is above 2^63
+  const unsigned long long y0 = (unsigned long long)fixed_point<BITS>(v0, emax) + C;
+  const unsigned long long y1 = (unsigned long long)fixed_point<BITS>(v1, emax) + C;
 #pragma unroll
   for (int t = 0; t < S; ++t) {
     const int s = DB * (S - 1 - t);
@@ -747,8 +750,9 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
                               TcShared& ts) {
   constexpr int G = S / 4;                 // stacks of four A planes
   constexpr int BITS = DB * S - 2;
-  // K accumulated in a TMEM cell before it is read: exactly (integers below
-  // 2^24, at most G products of 2^(2 DB - 2) per K step) for emulated FP64;
+  // K accumulated in a TMEM cell before it is read: exactly (integers of
+  // magnitude at most 2^24, at most G products of 2^(2 DB - 2) per K step)
+  // for emulated FP64;
   // the FP32-class mode only needs FP32 accumulation
   constexpr int KMAX = S == 8 ? (1 << 24) / (G << (2 * DB - 2)) : 4096;
   constexpr int ROWS = 32 * S;             // rows of the A stacks and of the B concatenation
@@ -756,7 +760,7 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
   // k2 = E_i + F_j - kScale: X_a X_b summed over the kept levels is
   // 2^(DB (S - 1)) V with V = sum_L S_L 2^(DB (S - 1 - L))
   constexpr int kScale = 2044 + 2 * BITS - DB * (S - 1);
-  static_assert((S == 8 && DB == 7) || (S == 4 && DB == 8), "digit formats of the two modes");
+  static_assert((S == 8 || S == 4) && DB == 8, "digit formats of the two modes");
   static_assert(S == 4 || KMAX >= TC_KS, "exact chunk");
   static_assert(32 * 4 * 32 * 16 <= 2 * TC_STAGE_BYTES_MAX, "drain buffer fits the staging region");
   uint8_t* stage = reinterpret_cast<uint8_t*>(smem);
@@ -1206,7 +1210,7 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
   double acc[TM][TN];
   if (tk.op != OP_TRTRI) {
     if constexpr (TC && TM == 2 && TN == 4) {  // reduced-precision parts are <= 32 x 32 sub-tiles
-      if (tk.prec == PREC_EMU64) accumulate_tc<8, 7>(p, tk, sb, acc, smem, *ts);
+      if (tk.prec == PREC_EMU64) accumulate_tc<8, 8>(p, tk, sb, acc, smem, *ts);
       else if (tk.prec == PREC_FP32X) accumulate_tc<4, 8>(p, tk, sb, acc, smem, *ts);
       else accumulate<TM, TN>(p, tk, sb, acc, As, Bs);
     } else {
