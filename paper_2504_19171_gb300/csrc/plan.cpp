@@ -118,6 +118,12 @@ struct Builder {
     else if (mode == PM_ROWS4 && t.m > 32) { t.pmode = PM_ROWS2; t.parts = 2; }
     else if (mode == PM_QUAD4 && t.m > 32 && t.n > 32) { t.pmode = PM_QUAD4; t.parts = 4; }
     else if (mode == PM_TRI3 && t.m > 32 && t.m == t.n) { t.pmode = PM_TRI3; t.parts = 3; }
+    else if (mode == PM_ROWS8 && t.m > 8 && t.m <= 32) { t.pmode = PM_ROWS8; t.parts = (uint8_t)((t.m + 7) / 8); }
+    else if (mode == PM_TRI16 && t.m > 16 && t.m <= 32 && t.m == t.n) { t.pmode = PM_TRI16; t.parts = 3; }
+    else if (mode == PM_QUAD16 && t.m <= 32 && t.n > 16 && t.n <= 32) {
+      t.pmode = PM_QUAD16;
+      t.parts = t.m > 16 ? 4 : 2;  // parts 2 and 3 are the lower row of quadrants
+    }
   }
 
   // Parts of an off-diagonal phase-2 block task (tuning bits 2-3).
@@ -337,13 +343,51 @@ struct Builder {
     };
     const size_t nfused = 0;  // every update runs as its own (split) task
     size_t nchain = terms.size() - nfused;
-    int total_writers = (int)nchain + 1;
+    // The critical path's links run as small parts on more CTAs: the FP64
+    // newest update of a diagonal block as three quadrant tasks of 16 x 16
+    // parts, the final TRSM of the block right below a diagonal block as two
+    // tasks of 8-row parts (they write disjoint parts of the block)
+    const bool newest_fp64 = nchain > 0 && (s.prec == PREC_FP64 ||
+                                            (i == kq && terms[nchain - 1].k == kq && !tune_lower_diag(s.tune)));
+    const bool fine_newest = diag && m == n && m > 32 && newest_fp64;
+    const bool fine_final = !diag && dist == 1 && m > 32;
+    // writers of the block's chain counter `me` (strictly ordered); the
+    // quadrant tasks and the two final TRSM halves run side by side and
+    // signal counters of their own
+    int total_writers = (int)nchain + 1 - (fine_newest ? 1 : 0);
     lfinal[lidx(i, kq, r, cq)] = total_writers;
+    bool written = false;  // the block already holds an update (read it from L, not A)
+    int32_t qctr = -1;     // the quadrant tasks of the newest update
     for (size_t t = 0; t < nchain; ++t) {
+      if (fine_newest && t + 1 == nchain) {
+        const Seg sg = term_seg(terms[t]);
+        const int qr[3] = {0, 32, 32}, qc[3] = {0, 0, 32};
+        qctr = newctr(false);
+        for (int x = 0; x < 3; ++x) {
+          const int64_t off = qr[x] + (int64_t)qc[x] * ld_i;
+          Task tq = blank(OP_UPD, std::min(32, m - qr[x]), std::min(32, n - qc[x]));
+          tq.out = outref + off;
+          tq.ldo = ld_i;
+          tq.cin = (written ? outref : mkref(BUF_A, L.blk(i, kq, r, cq))) + off;
+          tq.ldc = ld_i;
+          split(tq, x == 1 ? PM_QUAD16 : PM_TRI16);
+          if (grow(i, r) - grow(terms[t].k, terms[t].c1) <= kUrgentReach) tq.flags |= TF_URGENT;
+          Seg sq = sg;
+          sq.a += qr[x];
+          sq.b += qc[x];
+          std::vector<Wait> w;
+          if (nwritten > 0) w.push_back({me, nwritten});
+          if (!written && serve) w.push_back({prep_ctr[kq], 1});
+          term_waits(terms[t], w);
+          emit(tq, {sq}, w, {qctr}, 0.0);
+        }
+        written = true;
+        continue;
+      }
       Task tk = blank(OP_UPD, m, n);
       tk.out = outref;
       tk.ldo = ld_i;
-      tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
+      tk.cin = written ? outref : mkref(BUF_A, L.blk(i, kq, r, cq));
       tk.ldc = ld_i;
       // a diagonal block only needs its lower quadrants; the newest update of
       // a block gates its TRSM / POTRF on the critical path: split it 4 ways
@@ -355,33 +399,62 @@ struct Builder {
       if (!(i == kq && terms[t].k == kq) || tune_lower_diag(s.tune)) lower_precision(tk);
       std::vector<Wait> w;
       if (nwritten > 0) w.push_back({me, nwritten});
-      if (nwritten == 0 && serve) w.push_back({prep_ctr[kq], 1});
+      if (!written && serve) w.push_back({prep_ctr[kq], 1});
       term_waits(terms[t], w);
       sym_block = diag;
       emit(tk, {term_seg(terms[t])}, w, {me}, 0.0);
       ++nwritten;
+      written = true;
     }
     // final task
     std::vector<Seg> segs;
     std::vector<Wait> w;
     if (nwritten > 0) w.push_back({me, nwritten});
-    if (nwritten == 0 && serve) w.push_back({prep_ctr[kq], 1});
+    if (qctr >= 0) w.push_back({qctr, 3});
+    if (!written && serve) w.push_back({prep_ctr[kq], 1});
     for (size_t t = nchain; t < terms.size(); ++t) {
       segs.push_back(term_seg(terms[t]));
       term_waits(terms[t], w);
+    }
+    if (fine_final) {
+      // the two halves signal a counter of their own, which replaces the
+      // block's chain counter for every later reader (both are predecessors)
+      const int32_t dctr = lctr[lidx(kq, kq, cq, cq)];
+      w.push_back({dctr, lfinal[lidx(kq, kq, cq, cq)]});
+      const int32_t fctr = newctr(false);
+      if (kind == PLAN_FUSED) colblocks[kq]++;  // two final tasks signal the column
+      for (int h = 0; h < 2; ++h) {
+        const int r0 = 32 * h;
+        Task tq = blank(OP_TRSM_RLT, std::min(32, m - r0), n);
+        split(tq, PM_ROWS8);
+        tq.flags |= TF_URGENT;
+        tq.out = outref + r0;
+        tq.ldo = ld_i;
+        tq.cin = (written ? outref : mkref(BUF_A, L.blk(i, kq, r, cq))) + r0;
+        tq.ldc = ld_i;
+        tq.aux = mkref(BUF_L, L.blk(kq, kq, cq, cq));
+        tq.ldx = L.rows(kq);
+        std::vector<Seg> sh = segs;
+        for (Seg& g : sh) g.a += r0;
+        std::vector<int32_t> sig{fctr};
+        if (kind == PLAN_FUSED) sig.push_back(colfinal[kq]);
+        emit(tq, sh, w, sig, 2.0 * n * kSweepStepNs);
+      }
+      lctr[lidx(i, kq, r, cq)] = fctr;
+      lfinal[lidx(i, kq, r, cq)] = 2;
+      return;
     }
     Task tk = blank(diag ? OP_POTRF : OP_TRSM_RLT, m, n);
     if (!diag) split(tk, PM_ROWS4);
     if (diag || dist <= kUrgentReach) tk.flags |= TF_URGENT;
     tk.out = outref;
     tk.ldo = ld_i;
-    tk.cin = nwritten == 0 ? mkref(BUF_A, L.blk(i, kq, r, cq)) : outref;
+    tk.cin = written ? outref : mkref(BUF_A, L.blk(i, kq, r, cq));
     tk.ldc = ld_i;
     std::vector<int32_t> sig{me};
     double epi;
     if (diag) {
       tk.diag = ndiag++;
-      tk.zrows = cq * FB;
       tk.gcol = kq * s.b + cq * FB;
       epi = 3.0 * m * kSweepStepNs;
     } else {
@@ -393,6 +466,19 @@ struct Builder {
     }
     if (kind == PLAN_FUSED) sig.push_back(colfinal[kq]);
     emit(tk, segs, w, sig, epi);
+    if (diag && cq > 0) {
+      // L's strict upper part in this block column of the diagonal tile: no
+      // task reads it, so it is written by a task of its own, off the
+      // critical path (after the request's A in a served launch, which
+      // builds A in place in L)
+      Task z = blank(OP_ZERO, m, n);
+      z.out = outref;
+      z.ldo = ld_i;
+      z.zrows = cq * FB;
+      std::vector<Wait> zw;
+      if (serve) zw.push_back({prep_ctr[kq], 1});
+      emit(z, {}, zw, {}, 0.08 * z.zrows * n);
+    }
   }
 
   // ------------------------------------------------------------ selinv ----
@@ -855,8 +941,8 @@ int check_plan(const Plan& p) {
     if (tk.wait0 < 0 || tk.nwait < 0 || (int64_t)tk.wait0 + tk.nwait > (int64_t)p.waits.size()) return STILES_ERR_PLAN;
     if (tk.seg0 < 0 || tk.nseg < 0 || (int64_t)tk.seg0 + tk.nseg > (int64_t)p.segs.size()) return STILES_ERR_PLAN;
     if (tk.sig0 < 0 || tk.nsig < 0 || (int64_t)tk.sig0 + tk.nsig > (int64_t)p.sigs.size()) return STILES_ERR_PLAN;
-    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_PREP) return STILES_ERR_PLAN;
-    if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_TILE32 || tk.prec > PREC_FP32X) return STILES_ERR_PLAN;
+    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_ZERO) return STILES_ERR_PLAN;
+    if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_QUAD16 || tk.prec > PREC_FP32X) return STILES_ERR_PLAN;
     for (int q = 0; q < tk.nwait; ++q) {
       const Wait& w = p.waits[tk.wait0 + q];
       if (w.ctr < 0 || w.ctr >= p.nctr) return STILES_ERR_PLAN;
@@ -912,6 +998,12 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
         return bad("PREP out of bounds", t);
       continue;
     }
+    if (tk.op == OP_ZERO) {  // zrows x n above the block
+      if (tk.parts != 1 || tk.nseg != 0 || tk.zrows < 1 || tk.n < 1 ||
+          !in(tk.out, -(int64_t)tk.zrows, -1 + (int64_t)(tk.n - 1) * tk.ldo))
+        return bad("zeroed rows out of bounds", t);
+      continue;
+    }
     for (int q = 0; q < tk.parts; ++q) {
       int r0 = 0, c0 = 0, rm = tk.m, cn = tk.n;
       switch (tk.pmode) {
@@ -924,11 +1016,20 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
           r0 = 32 * (q % pr); c0 = 32 * (q / pr);
           break;
         }
+        case PM_ROWS8: r0 = 8 * q; rm = std::min(8, tk.m - r0); break;
+        case PM_TRI16: r0 = q == 0 ? 0 : 16; c0 = q == 2 ? 16 : 0; break;
+        case PM_QUAD16: r0 = 16 * (q >> 1); c0 = 16 * (q & 1); break;
         default: break;
       }
       if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3 || tk.pmode == PM_TILE32) {
         rm = std::min(32, tk.m - r0); cn = std::min(32, tk.n - c0);
+      } else if (tk.pmode == PM_TRI16 || tk.pmode == PM_QUAD16) {
+        rm = std::min(16, tk.m - r0); cn = std::min(16, tk.n - c0);
       }
+      if ((tk.pmode == PM_ROWS8 && tk.m > 32) || ((tk.pmode == PM_TRI16 || tk.pmode == PM_QUAD16) && (tk.m > 32 || tk.n > 32)))
+        return bad("fine part mode on a block larger than 32", t);
+      if ((tk.pmode == PM_TRI16 || tk.pmode == PM_QUAD16) && tk.prec != PREC_FP64)
+        return bad("16 x 16 parts on a reduced-precision task", t);
       if (tk.prec == PREC_EMU64 && (rm > 32 || cn > 32)) return bad("emulated task part larger than 32 x 32", t);
       if (tk.prec != PREC_FP64 && tk.op != OP_UPD && tk.op != OP_NEG && tk.op != OP_STORE && tk.op != OP_SYMUPD)
         return bad("reduced precision on a triangular task", t);
@@ -953,8 +1054,6 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
       if (tk.op == OP_SYMUPD && !(tk.flags & TF_SYM_DIAG) &&
           !in(tk.aux, c0 + (int64_t)r0 * tk.ldx, c1 + (int64_t)r1 * tk.ldx))
         return bad("mirror out of bounds", t);
-      if (tk.op == OP_POTRF && tk.zrows > 0 && !in(tk.out, -(int64_t)tk.zrows, -1 + (int64_t)(tk.n - 1) * tk.ldo))
-        return bad("zeroed rows out of bounds", t);
       if (tk.op == OP_POTRF && (tk.diag < 0 || tk.diag >= p.ndiag)) return bad("logdet slot out of range", t);
     }
   }

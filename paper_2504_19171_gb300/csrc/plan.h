@@ -39,6 +39,8 @@ enum Op : uint8_t {
   OP_PREP = 8,      // served requests: one tile column of A from the shape's base values and the
                     // request's (rho, tau): band entries x rho, arrow entries as they are,
                     // diagonal tau + rho rb[i] + ra[i] (rb / ra = band / arrow absolute row sums)
+  OP_ZERO = 9,      // the zrows x n block above out (L's strict upper part in a diagonal tile's
+                    // block column) set to zero; off the factorization's critical path
 };
 
 // How a task's output block is divided among CTAs (each part runs as its own
@@ -50,6 +52,9 @@ enum PartMode : uint8_t {
   PM_TRI3 = 3,   // quadrants (0,0), (1,0), (1,1): a diagonal block's lower part
   PM_ROWS4 = 4,  // rows [0,16), [16,32), [32,48), [48,64)
   PM_TILE32 = 5, // a grid of at most 2 x 2 sub-tiles of at most 32 x 32 (parts = row tiles x column tiles)
+  PM_ROWS8 = 6,  // rows [0,8), [8,16), [16,24), [24,32) of a block of at most 32 rows
+  PM_TRI16 = 7,  // quadrants (0,0), (1,0), (1,1) of 16 x 16: the lower part of a square block of at most 32
+  PM_QUAD16 = 8, // the 16 x 16 quadrants (0,0), (0,1), (1,0), (1,1) of a block of at most 32 x 32
 };
 
 // Arithmetic of a task's block products (its epilogue is always FP64).
@@ -91,7 +96,7 @@ struct Task {        // 64 bytes
   uint8_t op;
   uint8_t flags;     // TaskFlag bits
   int32_t diag;      // POTRF: index of its logdet partial sum
-  int32_t zrows;     // POTRF: rows above the block in its tile column to zero (L's strict upper part)
+  int32_t zrows;     // ZERO: rows above the block in its tile column to zero (L's strict upper part)
   int32_t gcol;      // POTRF: 0-based global column of the block's first pivot
   uint8_t parts;     // 1..4 queue entries (see PartMode)
   uint8_t pmode;

@@ -440,11 +440,17 @@ __device__ __forceinline__ Sub sub_of(const Task& tk, int q) {
       sb.c0 = 32 * (q / pr);
       break;
     }
+    case PM_ROWS8: sb.r0 = 8 * q; sb.rm = min(8, tk.m - sb.r0); break;
+    case PM_TRI16: sb.r0 = q == 0 ? 0 : 16; sb.c0 = q == 2 ? 16 : 0; break;
+    case PM_QUAD16: sb.r0 = 16 * (q >> 1); sb.c0 = 16 * (q & 1); break;
     default: break;
   }
   if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3 || tk.pmode == PM_TILE32) {
     sb.rm = min(32, tk.m - sb.r0);
     sb.cn = min(32, tk.n - sb.c0);
+  } else if (tk.pmode == PM_TRI16 || tk.pmode == PM_QUAD16) {
+    sb.rm = min(16, tk.m - sb.r0);
+    sb.cn = min(16, tk.n - sb.c0);
   }
   return sb;
 }
@@ -1060,6 +1066,37 @@ __device__ __forceinline__ void trsm_rows_lt16(double* X, const double* Tn, cons
   }
 }
 
+// The same for m <= 8 (the parts of a row-split block on the factorization's
+// critical path): two rows per warp, 16 lanes per row, so that a lane applies
+// at most four columns per step.
+__device__ __forceinline__ void trsm_rows_lt8(double* X, const double* Tn, const double* rcp, int m, int n) {
+  static_assert(FB == 64, "16 lanes x 4 columns per row");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = warp * 2 + (lane & 1), ph = lane >> 1;
+  const bool own = r < m;
+  double y[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = ph + 16 * q;
+    y[q] = own && c < n ? X[r * LDS + c] : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < FB; ++j) {
+    if (j >= n) break;
+    const double yj = __shfl_sync(0xffffffffu, y[j >> 4], (lane & 1) + 2 * (j & 15));
+#pragma unroll
+    for (int q = j >> 4; q < 4; ++q) {
+      const int c = ph + 16 * q;
+      if (c > j) y[q] = fma(-yj, Tn[c * LDS + j], y[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = ph + 16 * q;
+    if (own && c < n) X[r * LDS + c] = y[q] * rcp[c * LDS];
+  }
+}
+
 // X (m x n) <- T^{-1} X, T lower m x m, rcp[j*LDS] = 1 / T[j][j]. Columns are
 // independent; warp w owns columns 4q + w (interleaved, so that the
 // triangular work of an inverse is balanced). `lower` skips the columns c > j
@@ -1291,7 +1328,8 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
         for (int c = warp + 1; c < n; c += NTHREADS / 32)
           for (int j = lane; j < c; j += 32) T[c * LDS + j] *= rcp[j * LDS];
         __syncthreads();
-        trsm_rows_lt16(X, T, rcp, sb.rm, n);
+        if (sb.rm <= 8) trsm_rows_lt8(X, T, rcp, sb.rm, n);
+        else trsm_rows_lt16(X, T, rcp, sb.rm, n);
       } else {
         trsm_rows_lt(X, T, rcp, sb.rm, n);
       }
@@ -1307,11 +1345,6 @@ __device__ void run_sub(const KParams& p, const Task& tk, const Sub& sb, double*
             __syncthreads();
             const int bad = potrf_smem(X, n);
             store_sub(p, tk, sb, X, true);
-            if (tk.zrows > 0) {  // strict upper part of L's diagonal tile in this block column
-              double* Z = resolve(p, tk.out) - tk.zrows;
-              for (int e = tid; e < tk.zrows * n; e += NTHREADS)
-                Z[e % tk.zrows + (int64_t)(e / tk.zrows) * tk.ldo] = 0.0;
-            }
             // log of the pivots, summed in a fixed tree order
             double lg = tid < n ? log(X[tid * LDS + tid]) : 0.0;
 #pragma unroll
@@ -1394,16 +1427,31 @@ __device__ bool task_part_ok(const KParams& p, const Task& tk, const Sub& sb) {
     return false;
   if (tk.op == OP_SYMUPD && !(tk.flags & TF_SYM_DIAG) && !ref_ok(p, tk.aux, c0 + (int64_t)r0 * tk.ldx, c1 + (int64_t)r1 * tk.ldx))
     return false;
-  if (tk.op == OP_POTRF && tk.zrows > 0 && !ref_ok(p, tk.out, -(int64_t)tk.zrows, (int64_t)(tk.n - 1) * tk.ldo))
-    return false;
   return true;
 }
 #endif
+
+// OP_ZERO: the zrows x n block above the task's output block (column-major,
+// leading dimension ldo) set to zero.
+__device__ void run_zero(const KParams& p, const Task& tk, int t) {
+#ifdef STILES_CHECKED
+  if (tk.zrows < 1 || tk.n < 1 || !ref_ok(p, tk.out, -(int64_t)tk.zrows, (int64_t)(tk.n - 1) * tk.ldo)) {
+    if (threadIdx.x == 0) check_fail(p, 7, t, 0);
+    return;
+  }
+#endif
+  double* Z = resolve(p, tk.out) - tk.zrows;
+  for (int e = threadIdx.x; e < tk.zrows * tk.n; e += NTHREADS) Z[e % tk.zrows + (int64_t)(e / tk.zrows) * tk.ldo] = 0.0;
+}
 
 template <bool TC>
 __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double* smem, TcShared* ts) {
   if (tk.op == OP_PREP) {
     run_prep(p, tk, t);
+    return;
+  }
+  if (tk.op == OP_ZERO) {
+    run_zero(p, tk, t);
     return;
   }
   const Sub sb = sub_of(tk, q);
@@ -1416,7 +1464,10 @@ __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double*
 #endif
   switch (tk.pmode) {
     case PM_ROWS2: run_sub<TC, 2, 8>(p, tk, sb, smem, ts); break;
-    case PM_ROWS4: run_sub<TC, 1, 8>(p, tk, sb, smem, ts); break;
+    case PM_ROWS4:
+    case PM_ROWS8: run_sub<TC, 1, 8>(p, tk, sb, smem, ts); break;
+    case PM_TRI16:
+    case PM_QUAD16: run_sub<TC, 1, 2>(p, tk, sb, smem, ts); break;
     case PM_QUAD4:
     case PM_TRI3:
     case PM_TILE32: run_sub<TC, 2, 4>(p, tk, sb, smem, ts); break;

@@ -191,3 +191,39 @@ def test_update_runs_parity(shape):
     assert rel_err(S_emu, Sr) < 1e-12
     for ld in (ld_fused, ld_split, ld_emu):
         assert abs(ld - ldr) < 1e-10 * abs(ldr)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", ["fused", "split", "inplace"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_strict_upper_of_diagonal_tiles(mode, precision):
+    """L's strict upper part in every diagonal tile is written as zero, and
+    A's is never read: both start as NaN (the whole L buffer, and the strict
+    upper triangles of A's diagonal tiles), the results still match the
+    oracle and L's strict upper triangles come out exactly zero."""
+    S = need_gpu()
+    import torch
+    M = W.random_arrowhead(6, 192, 2, 24, seed=11)  # three 64-column blocks per tile
+    Lr, Sr, ldr = O.selinv(M)
+    st = S.Stiles(M.nt, M.b, M.w, M.a, wait_budget_s=5.0, precision=precision).upload(M)
+    try:
+        lay = st.layout
+        for i in range(M.nt + (1 if M.a else 0)):
+            T = lay.tile_view(st.A, i, i)
+            T.copy_(torch.where(torch.ones_like(T, dtype=torch.bool).triu(1), torch.full_like(T, float("nan")), T))
+        st.L.fill_(float("nan"))
+        if mode == "fused":
+            st.factor_selinv()
+        else:
+            st.factor(inplace=(mode == "inplace"))
+            st.selinv()
+        torch.cuda.synchronize()
+        assert st.status()[0] == 0
+        L, Sg = st.L_tiles(), st.sigma_tiles()
+    finally:
+        st.close()
+    tol = FP64_TOL if precision == 0 else 1e-12
+    assert rel_err(L, Lr) < tol and rel_err(Sg, Sr) < tol
+    for i in range(M.nt + (1 if M.a else 0)):
+        U = np.triu(L[(i, i)], 1)
+        assert np.all(U == 0), (i, np.argwhere(U != 0)[:3])
