@@ -304,6 +304,21 @@ int stiles_debug_validate(int nt, int b, int band, int arrow, int which);
  * STILES_ERR_PLAN). Host only. */
 int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode);
 
+/* Test hook: build the plan `which` (as in stiles_plan_stats) and check it
+ * for races on the host: the table is replayed in its order and every two
+ * task parts that touch the same element of A, L, Sigma or the scratch
+ * tiles, one of them writing it, must be ordered by the dependency graph
+ * (parts of one task run side by side and must not conflict at all). The
+ * accesses follow the kernel's: operand regions of each segment, the input
+ * sub-block, the lower triangle of a triangular block, the output sub-block,
+ * SYMUPD's mirror, the rows a ZERO task clears. plant = 1 removes every
+ * predecessor of the last POTRF that has some before the check (a planted
+ * race, expected to be found). Returns STILES_OK, STILES_ERR_PLAN (the first
+ * race printed to stderr) or STILES_ERR_INVALID_ARG (bad arguments, or a
+ * plan of more than 16384 tasks). Host only; memory grows with the buffers
+ * (12 bytes per element) -- meant for small shapes. */
+int stiles_debug_race_check(int nt, int b, int band, int arrow, int which, int plant);
+
 /* Test hook: make the handle's plan `which` unsatisfiable on the device (one
  * task waits for one more predecessor than it has) without the host check,
  * so that a launch must end with STILES_ERR_TIMEOUT once the wait budget

@@ -1094,4 +1094,180 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
   return 0;
 }
 
+
+// ---------------------------------------------------------- race check ----
+// Host check of a task table (tests): replays the table in its order (a
+// topological order of the successor graph) and requires every two task
+// parts that touch the same element, one of them writing it, to be ordered
+// by the graph -- parts of one task run side by side, so they must not
+// conflict at all. Accesses follow the kernel: each part reads its segments'
+// operand regions, its input sub-block, the lower triangle of a triangular
+// block, and writes its output sub-block (plus the mirror of SYMUPD and the
+// rows above a ZERO task's block). Element granularity; plans of at most
+// 16384 tasks. plant = 1 removes the predecessors of the last POTRF that has
+// some (a planted race the check must find). Returns 0, STILES_ERR_PLAN (the
+// first race printed to stderr) or STILES_ERR_INVALID_ARG.
+namespace {
+
+struct PartRect {
+  int r0, c0, rm, cn;
+};
+
+PartRect part_rect(const Task& tk, int q) {
+  PartRect x{0, 0, tk.m, tk.n};
+  switch (tk.pmode) {
+    case PM_ROWS2: x.r0 = 32 * q; x.rm = std::min(32, tk.m - x.r0); break;
+    case PM_ROWS4: x.r0 = 16 * q; x.rm = std::min(16, tk.m - x.r0); break;
+    case PM_ROWS8: x.r0 = 8 * q; x.rm = std::min(8, tk.m - x.r0); break;
+    case PM_QUAD4: x.r0 = 32 * (q & 1); x.c0 = 32 * (q >> 1); break;
+    case PM_TRI3: x.r0 = q == 0 ? 0 : 32; x.c0 = q == 2 ? 32 : 0; break;
+    case PM_TRI16: x.r0 = q == 0 ? 0 : 16; x.c0 = q == 2 ? 16 : 0; break;
+    case PM_QUAD16: x.r0 = 16 * (q >> 1); x.c0 = 16 * (q & 1); break;
+    case PM_TILE32: {
+      const int pr = tk.m > 32 ? 2 : 1;
+      x.r0 = 32 * (q % pr);
+      x.c0 = 32 * (q / pr);
+      break;
+    }
+    default: break;
+  }
+  if (tk.pmode == PM_QUAD4 || tk.pmode == PM_TRI3 || tk.pmode == PM_TILE32) {
+    x.rm = std::min(32, tk.m - x.r0);
+    x.cn = std::min(32, tk.n - x.c0);
+  } else if (tk.pmode == PM_TRI16 || tk.pmode == PM_QUAD16) {
+    x.rm = std::min(16, tk.m - x.r0);
+    x.cn = std::min(16, tk.n - x.c0);
+  }
+  return x;
+}
+
+class RaceCheck {
+ public:
+  RaceCheck(const Plan& p, int64_t lim, const std::vector<std::vector<int32_t>>& preds)
+      : p_(p), lim_(lim), n_((int)p.tasks.size()), words_((n_ + 63) / 64) {
+    anc_.assign((size_t)n_ * words_, 0ull);
+    for (int t = 0; t < n_; ++t)
+      for (int32_t q : preds[t]) {
+        uint64_t* a = &anc_[(size_t)t * words_];
+        const uint64_t* b = &anc_[(size_t)q * words_];
+        for (int w = 0; w < words_; ++w) a[w] |= b[w];
+        a[q >> 6] |= 1ull << (q & 63);
+      }
+    for (int b = 0; b < 4; ++b) {
+      lw_[b].assign(lim, -1);
+      head_[b].assign(lim, -1);
+    }
+  }
+  bool before(int a, int b) const { return (anc_[(size_t)b * words_ + (a >> 6)] >> (a & 63)) & 1; }
+
+  // one access of part `id` (4 task + part) to element `off` of buffer `buf`
+  bool access(int buf, int64_t off, int id, bool write) {
+    if (buf < 0 || buf > 3 || off < 0 || off >= lim_) return fail("access outside the buffers", id, -1, buf, off);
+    const int t = id >> 2;
+    const int w = lw_[buf][off];
+    if (w >= 0 && w != id && !before(w >> 2, t)) return fail(write ? "unordered writes" : "read not ordered after the write", w, id, buf, off);
+    if (!write) {
+      // keep the readers since the last write that no later reader descends from
+      int* link = &head_[buf][off];
+      while (*link >= 0) {
+        const int r = pool_[*link].first;
+        if (r == id) return true;
+        if (r >> 2 != t && before(r >> 2, t)) *link = pool_[*link].second;
+        else link = &pool_[*link].second;
+      }
+      pool_.push_back({id, head_[buf][off]});
+      head_[buf][off] = (int)pool_.size() - 1;
+      return true;
+    }
+    for (int e = head_[buf][off]; e >= 0; e = pool_[e].second) {
+      const int r = pool_[e].first;
+      if (r != id && !before(r >> 2, t)) return fail("write not ordered after a read", r, id, buf, off);
+    }
+    head_[buf][off] = -1;
+    lw_[buf][off] = id;
+    return true;
+  }
+  // rows r0 .. r0+rm-1 of columns c0 .. c0+cn-1 of the block at ref (leading dimension ld)
+  bool rect(int64_t ref, int ld, int r0, int rm, int c0, int cn, int id, bool write, bool lower = false) {
+    const int buf = (int)(ref >> BUF_SHIFT);
+    const int64_t base = ref & OFF_MASK;
+    for (int c = c0; c < c0 + cn; ++c)
+      for (int r = r0; r < r0 + rm; ++r)
+        if (!lower || r >= c)
+          if (!access(buf, base + r + (int64_t)c * ld, id, write)) return false;
+    return true;
+  }
+  bool task_part(int t, int q) {
+    const Task& tk = p_.tasks[t];
+    const int id = 4 * t + q;
+    if (tk.op == OP_ZERO) return rect(tk.out, tk.ldo, -tk.zrows, tk.zrows, 0, tk.n, id, true);
+    const PartRect x = part_rect(tk, q);
+    if (x.rm <= 0 || x.cn <= 0) return true;
+    for (int g = tk.seg0; g < tk.seg0 + tk.nseg; ++g) {
+      const Seg& sg = p_.segs[g];
+      const bool ta = sg.trans & 1, tb = sg.trans & 2;
+      // op(A) rows r0 .. r0+rm-1, op(B) columns c0 .. c0+cn-1, K = 0 .. k-1
+      if (ta ? !rect(sg.a, sg.lda, 0, sg.k, x.r0, x.rm, id, false) : !rect(sg.a, sg.lda, x.r0, x.rm, 0, sg.k, id, false))
+        return false;
+      if (tb ? !rect(sg.b, sg.ldb, x.c0, x.cn, 0, sg.k, id, false) : !rect(sg.b, sg.ldb, 0, sg.k, x.c0, x.cn, id, false))
+        return false;
+    }
+    const bool cin = tk.op == OP_UPD || tk.op == OP_POTRF || tk.op == OP_TRSM_RLT || tk.op == OP_SYMUPD;
+    if (cin && !rect(tk.cin, tk.ldc, x.r0, x.rm, x.c0, x.cn, id, false)) return false;
+    if (tk.op == OP_TRSM_RLT && !rect(tk.aux, tk.ldx, 0, tk.n, 0, tk.n, id, false, true)) return false;
+    if ((tk.op == OP_TRSM_LLN || tk.op == OP_TRTRI) && !rect(tk.aux, tk.ldx, 0, tk.m, 0, tk.m, id, false, true))
+      return false;
+    if (!rect(tk.out, tk.ldo, x.r0, x.rm, x.c0, x.cn, id, true)) return false;
+    if (tk.op == OP_SYMUPD && !((tk.flags & TF_SYM_DIAG) && x.r0 == x.c0)) {
+      // the transpose of the sub-block: inside the same block, or the mirror block
+      const bool dblk = tk.flags & TF_SYM_DIAG;
+      if (!rect(dblk ? tk.out : tk.aux, dblk ? tk.ldo : tk.ldx, x.c0, x.cn, x.r0, x.rm, id, true)) return false;
+    }
+    return true;
+  }
+  bool fail(const char* what, int a, int b, int buf, int64_t off) {
+    const int ta = a >= 0 ? a >> 2 : -1, tb = b >= 0 ? b >> 2 : -1;
+    fprintf(stderr, "race_check: %s: task %d part %d (op %d) and task %d part %d (op %d), buffer %d element %lld\n",
+            what, ta, a & 3, ta >= 0 ? (int)p_.tasks[ta].op : -1, tb, b & 3, tb >= 0 ? (int)p_.tasks[tb].op : -1,
+            buf, (long long)off);
+    return false;
+  }
+
+ private:
+  const Plan& p_;
+  int64_t lim_;
+  int n_, words_;
+  std::vector<uint64_t> anc_;
+  std::vector<int> lw_[4], head_[4];
+  std::vector<std::pair<int, int>> pool_;
+};
+
+}  // namespace
+
+int race_check_plan(const Plan& p, int64_t lim, int plant) {
+  const int n = (int)p.tasks.size();
+  if (n > 16384 || (int64_t)p.succ_off.size() != (int64_t)n + 1) return STILES_ERR_INVALID_ARG;
+  std::vector<std::vector<int32_t>> preds(n);
+  for (int t = 0; t < n; ++t)
+    for (int e = p.succ_off[t]; e < p.succ_off[t + 1]; ++e) {
+      const int s = p.succ[e];
+      if (s <= t || s >= n) return STILES_ERR_PLAN;  // the table order must be topological
+      preds[s].push_back(t);
+    }
+  if (plant == 1) {
+    int victim = -1;
+    for (int t = 0; t < n; ++t)
+      if (p.tasks[t].op == OP_POTRF && !preds[t].empty()) victim = t;
+    if (victim < 0) return STILES_ERR_INVALID_ARG;
+    preds[victim].clear();
+  }
+  for (const Task& tk : p.tasks)
+    if (tk.op == OP_PREP) return STILES_ERR_INVALID_ARG;  // request-server tables are not modelled
+  RaceCheck rc(p, lim, preds);
+  for (int t = 0; t < n; ++t)
+    for (int q = 0; q < std::max(1, (int)p.tasks[t].parts); ++q)
+      if (!rc.task_part(t, q)) return STILES_ERR_PLAN;
+  return 0;
+}
+
 }  // namespace stiles

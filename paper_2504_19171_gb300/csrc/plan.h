@@ -215,6 +215,8 @@ int validate_plan(const Plan& p, const Shape& s, int kind);
 // The same with an explicit buffer length (doubles in each of A, L, Sigma and
 // the scratch's packed part), for batch plans.
 int validate_plan_len(const Plan& p, int64_t buf_doubles, int kind);
+// Host race check of a plan (see plan.cpp); plant = 1 plants a race first.
+int race_check_plan(const Plan& p, int64_t buf_doubles, int plant);
 
 // Fused task table of one shape for the request server: as the fused plan,
 // plus one OP_PREP task per tile column that writes the request's A (in the

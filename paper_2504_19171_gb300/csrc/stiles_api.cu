@@ -462,6 +462,17 @@ extern "C" int stiles_debug_validate(int nt, int b, int band, int arrow, int whi
   return rc ? rc : validate_plan(p, sh, kind);
 }
 
+extern "C" int stiles_debug_race_check(int nt, int b, int band, int arrow, int which, int plant) {
+  const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
+  if (kind < 0 || kind > 2 || prec > PREC_FP32X || !tune_valid(tune) || nt < 1 || b < 1 || band < 0 || arrow < 0 ||
+      plant < 0 || plant > 1)
+    return STILES_ERR_INVALID_ARG;
+  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune, sel0};
+  Plan p;
+  const int rc = build_plan(sh, (PlanKind)kind, 304, &p);
+  return rc ? rc : race_check_plan(p, Layout(sh).doubles(), plant);
+}
+
 extern "C" int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode) {
   if (which < 0 || which > 2 || nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
   Plan p;

@@ -54,7 +54,7 @@ EXPORTS = [
     "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
     "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status", "stiles_server_submit_values",
-    "stiles_debug_occupancy",
+    "stiles_debug_occupancy", "stiles_debug_race_check",
 ]
 
 
@@ -82,6 +82,7 @@ def _load() -> ctypes.CDLL:
         "stiles_set_option": [vp, i32, i64],
         "stiles_plan_stats": [i32, i32, i32, i32, i32, i32, P(i64)],
         "stiles_debug_check_corrupted": [i32, i32, i32, i32, i32, i32],
+        "stiles_debug_race_check": [i32, i32, i32, i32, i32, i32],
         "stiles_debug_break_plan": [vp, i32],
         "stiles_destroy": [vp],
         "stiles_strerror": [i32],
@@ -221,6 +222,12 @@ def stiles_plan_stats(nt: int, b: int, band: int, arrow: int, which: int, worker
 
 def stiles_debug_validate(nt: int, b: int, band: int, arrow: int, which: int, precision: int = STILES_FP64) -> int:
     return _lib.stiles_debug_validate(nt, b, band, arrow, which + 16 * precision)
+
+
+def stiles_debug_race_check(nt: int, b: int, band: int, arrow: int, which: int, precision: int = STILES_FP64,
+                            plant: int = 0) -> int:
+    """Host race check of a plan (0 = race-free; see include/stiles.h)."""
+    return _lib.stiles_debug_race_check(nt, b, band, arrow, which + 16 * precision, plant)
 
 
 def stiles_debug_check_corrupted(nt: int, b: int, band: int, arrow: int, which: int, mode: int) -> int:
