@@ -50,11 +50,11 @@ VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (tcgen05)", "digits": 8, "pro
                     "fp32x": {"pipe": "bf16 tensor (tcgen05)", "digits": 4, "products": 10}}
 
 # DRAM traffic of the persistent kernel per launch, from ncu captures of the
-# nt = 8 and nt = 16 cases of the same matrix family (0.809 GB and 2.164 GB):
+# nt = 8 and nt = 16 cases of the same matrix family (0.790 GB and 2.112 GB):
 # the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
-TRAFFIC = {"sources_sha": "7ccf1b214a31ed44", "bytes_per_launch": 33.33e9}
+TRAFFIC = {"sources_sha": "05a409edd51d7494", "bytes_per_launch": 32.51e9}
 
 
 def measured_peaks() -> dict:
