@@ -43,11 +43,12 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # SIMT FP32 FMA: 128 lanes per SM per clock.
 FP32_SIMT_PEAK_TFLOPS = 2 * 128 * 152 * 2.070e9 / 1e12
 # Low-precision products per FP64-equivalent multiply-add of each reduced mode
-# (the digit-pair products of the split-precision scheme: with s digits per
+# as the tensor cores run them (the plane pairs of the split: with s planes per
 # operand the levels t + u <= s - 1 are kept, s (s + 1) / 2 products), and the
-# pipe that runs them.
+# pipe that runs them. EMU64: 8 fixed-point digits; FP32X: 3 bf16 pieces of
+# the FP32 value in the same 4-plane layout (the fourth plane is zero).
 VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (tcgen05)", "digits": 8, "products": 36},
-                    "fp32x": {"pipe": "bf16 tensor (tcgen05)", "digits": 4, "products": 10}}
+                    "fp32x": {"pipe": "bf16 tensor (tcgen05)", "digits": 3, "products": 10}}
 
 # DRAM traffic of the persistent kernel per launch, from ncu captures of the
 # nt = 8 and nt = 16 cases of the same matrix family (0.790 GB and 2.112 GB):

@@ -551,7 +551,10 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // 2^(2 DB - 2); products of levels L = t + u <= S - 1 are kept. Emulated FP64
 // uses S = 8 digits of DB = 8 bits (|X| < 2^62: entries down to 2^-9 of their
 // row maximum keep all 53 bits, the dropped levels weigh below 2^-56 of the
-// leading product), the FP32-class mode S = 4 digits of 8 bits (32 bits).
+// leading product). The FP32-class mode uses no shared exponent: every entry
+// becomes its FP32 value (rounded toward zero) written as three bf16 pieces
+// that keep their own exponents (piece_pairs), in the same four-plane layout
+// with a zero fourth plane; its cells hold ordinary FP32 sums.
 //
 // Tensor-core layout. D has M = 128 rows, made from a 32-row part by
 // stacking four digit planes of A: stack g (g < G = S / 4) holds plane
@@ -565,10 +568,12 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // 2^24 / (G 2^14) = 512 of K.
 // Before that much K has been accumulated (or at the end of the task) the
 // cells of levels <= S - 1 are read -- warp p reads lane block p -- and
-// combined per output: exactly in two 64-bit halves for emulated FP64, in
-// FP32 for the FP32-class mode. The result, scaled by 2^(E_i + F_j - bias),
-// is added to the part's FP64 value.
-// Non-finite operands (biased exponent 0x7ff) make their row or column NaN.
+// combined per output: exactly in two 64-bit halves for emulated FP64, then
+// scaled by 2^(E_i + F_j - bias); summed in FP32 for the FP32-class mode. The
+// result is added to the part's FP64 value.
+// Non-finite operands make their row or column NaN (emulated FP64: biased
+// exponent 0x7ff; FP32-class: NaN pieces, also for values beyond the FP32
+// range).
 
 constexpr int TC_KS = 32;           // K per staging buffer (two MMA K steps)
 constexpr uint32_t TC_COLS = 256;   // TMEM columns per CTA (two CTAs per SM share 512)
@@ -685,6 +690,41 @@ __device__ __forceinline__ void digit_pairs(double v0, double v1, int emax, uint
   }
 }
 
+// FP32-class operands: the value rounded to nearest FP32 (ties away from
+// zero), built from the double's bits without an FP64 instruction: half a
+// unit of the 23rd fraction bit is added to the bit pattern (a carry moves
+// into the exponent as it should), then sign, exponent rebiased and the top
+// 23 fraction bits are taken. Below the FP32 normal range it is zero, above
+// it infinity; an infinity or NaN in gives NaN.
+__device__ __forceinline__ uint32_t fp32_bits_of(double v) {
+  const unsigned long long b0 = (unsigned long long)__double_as_longlong(v);
+  if (((b0 >> 52) & 0x7ff) == 0x7ff) return 0x7fc00000u;
+  const unsigned long long b = b0 + (1ull << 28);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const int e = (int)((hi >> 20) & 0x7ff);
+  const uint32_t sgn = hi & 0x80000000u;
+  if (e < 1023 - 126) return sgn;
+  if (e > 1023 + 127) return sgn | 0x7f800000u;
+  return sgn | ((uint32_t)(e - 1023 + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+}
+
+// The FP32 values of a pair of K-adjacent operands (v0 at k, v1 at k + 1) as
+// three bf16 pieces each, packed in pairs like digit_pairs: piece t is the
+// value left after pieces < t, truncated to its top 8 significant bits, so
+// the three pieces sum to the FP32 value exactly and each keeps its own
+// exponent. The fourth plane is zero.
+__device__ __forceinline__ void piece_pairs(double v0, double v1, uint32_t (&w)[4]) {
+  float r0 = __uint_as_float(fp32_bits_of(v0)), r1 = __uint_as_float(fp32_bits_of(v1));
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t p0 = __float_as_uint(r0) & 0xffff0000u, p1 = __float_as_uint(r1) & 0xffff0000u;
+    w[t] = (p0 >> 16) | p1;
+    r0 -= __uint_as_float(p0);
+    r1 -= __uint_as_float(p1);
+  }
+  w[3] = 0u;
+}
+
 // Byte offset of element (row, k) (k even: a packed pair) in a staging
 // operand of canonical K-major core matrices: 8 rows x 8 K per 128 bytes,
 // TC_KS / 8 core matrices along K per 8-row group.
@@ -754,6 +794,9 @@ __device__ __forceinline__ void tc_load(const double* A, const double* B, const 
 template <int S, int DB>
 __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, double (&acc)[2][4], double* smem,
                               TcShared& ts) {
+  // FP32-class parts (S = 4) take per-element FP32 pieces (piece_pairs): no
+  // shared exponents, so no exponent pre-pass and no scaling at the drain
+  constexpr bool FLT = S == 4;
   constexpr int G = S / 4;                 // stacks of four A planes
   constexpr int BITS = DB * S - 2;
   // K accumulated in a TMEM cell before it is read: exactly (integers of
@@ -776,15 +819,17 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
   double* R = reinterpret_cast<double*>(stage + TC_RES_OFF);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // exponents of the rows of op(A) and columns of op(B) over all segments
-  if (tid < 64) rexp[tid] = 0;
-  __syncthreads();
-  for (int s = 0; s < tk.nseg; ++s) {
-    const Seg gs = load_seg(p, tk.seg0 + s);
-    const bool ta = gs.trans & 1, tb = gs.trans & 2;
-    const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
-    const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
-    max_exp_into(A, gs.lda, !ta, sb.rm, gs.k, rexp);
-    max_exp_into(B, gs.ldb, tb, sb.cn, gs.k, cexp);
+  if constexpr (!FLT) {
+    if (tid < 64) rexp[tid] = 0;
+    __syncthreads();
+    for (int s = 0; s < tk.nseg; ++s) {
+      const Seg gs = load_seg(p, tk.seg0 + s);
+      const bool ta = gs.trans & 1, tb = gs.trans & 2;
+      const double* A = resolve(p, gs.a) + (ta ? (int64_t)sb.r0 * gs.lda : (int64_t)sb.r0);
+      const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
+      max_exp_into(A, gs.lda, !ta, sb.rm, gs.k, rexp);
+      max_exp_into(B, gs.ldb, tb, sb.cn, gs.k, cexp);
+    }
   }
 #pragma unroll
   for (int js = 0; js < 8; ++js) R[lane * 33 + 4 * js + warp] = 0.0;
@@ -818,7 +863,8 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
           int i, kk;
           tc_slot(q, i, kk);
           uint32_t w[S];
-          digit_pairs<S, DB>(ca[2 * q], ca[2 * q + 1], rexp[i], w);
+          if constexpr (FLT) piece_pairs(ca[2 * q], ca[2 * q + 1], w);
+          else digit_pairs<S, DB>(ca[2 * q], ca[2 * q + 1], rexp[i], w);
 #pragma unroll
           for (int t = 0; t < S; ++t)
             *reinterpret_cast<uint32_t*>(sa + tc_off(128 * (t % G) + 32 * (t / G) + i, kk)) = w[t];
@@ -829,7 +875,8 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
           int j, kk;
           tc_slot(q, j, kk);
           uint32_t w[S];
-          digit_pairs<S, DB>(cb[2 * q], cb[2 * q + 1], cexp[j], w);
+          if constexpr (FLT) piece_pairs(cb[2 * q], cb[2 * q + 1], w);
+          else digit_pairs<S, DB>(cb[2 * q], cb[2 * q + 1], cexp[j], w);
 #pragma unroll
           for (int t = 0; t < S; ++t) *reinterpret_cast<uint32_t*>(sbuf + tc_off(32 * t + j, kk)) = w[t];
         }
@@ -900,7 +947,7 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
 #pragma unroll
             for (int c = 0; c < S; ++c) {
               const int L = G * warp + c;
-              if (L <= S - 1) v = fmaf(__uint_as_float(cell[c][x]), (float)(1 << (DB * (3 - L))), v);
+              if (L <= S - 1) v = FLT ? v + __uint_as_float(cell[c][x]) : fmaf(__uint_as_float(cell[c][x]), (float)(1 << (DB * (3 - L))), v);
             }
             partf[((4 * js + x) * 4 + warp) * 32 + lane] = v;
           }
@@ -927,11 +974,16 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
           for (int pb = 0; pb < 4; ++pb) f += partf[(j * 4 + pb) * 32 + lane];
           V = (double)f;
         }
-        const int er = rexp[lane], ec = cexp[j];
-        const int k2 = max(er, 1) + max(ec, 1) - kScale;
-        const double sc = (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
         double& r = R[lane * 33 + j];
-        r = (er == 0x7ff || ec == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll) : fma(V, sc, r);
+        if constexpr (FLT) {
+          r += V;
+        } else {
+          const int er = rexp[lane], ec = cexp[j];
+          const int k2 = max(er, 1) + max(ec, 1) - kScale;
+          const double sc =
+              (k2 >= -1022 && k2 <= 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52) : ldexp(1.0, k2);
+          r = (er == 0x7ff || ec == 0x7ff) ? __longlong_as_double(0x7ff8000000000000ll) : fma(V, sc, r);
+        }
       }
       tc::fence_before_sync();
       __syncthreads();  // TMEM reads done before the next MMAs; staging free again
