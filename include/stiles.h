@@ -319,6 +319,14 @@ int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, 
  * (12 bytes per element) -- meant for small shapes. */
 int stiles_debug_race_check(int nt, int b, int band, int arrow, int which, int plant);
 
+/* Test hook: the same race check for the request-server template of a shape
+ * (precision and tuning as in stiles_server_create): a served request's A is
+ * built in place in L by the template's PREP tasks, so A references alias L
+ * and each PREP task writes its whole tile column of L. plant as above.
+ * Returns STILES_OK, STILES_ERR_PLAN (first race on stderr) or
+ * STILES_ERR_INVALID_ARG. Host only; small shapes. */
+int stiles_debug_race_check_serve(int nt, int b, int band, int arrow, int precision, int tuning, int plant);
+
 /* Test hook: make the handle's plan `which` unsatisfiable on the device (one
  * task waits for one more predecessor than it has) without the host check,
  * so that a launch must end with STILES_ERR_TIMEOUT once the wait budget

@@ -1105,7 +1105,10 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
 // block, and writes its output sub-block (plus the mirror of SYMUPD and the
 // rows above a ZERO task's block). Element granularity; plans of at most
 // 16384 tasks. plant = 1 removes the predecessors of the last POTRF that has
-// some (a planted race the check must find). Returns 0, STILES_ERR_PLAN (the
+// some (a planted race the check must find). serve: a request-server
+// template, whose A is built in place in L (A references alias L) by PREP
+// tasks that write their whole tile column of L (their reads of the shape's
+// base values touch no buffer of the launch). Returns 0, STILES_ERR_PLAN (the
 // first race printed to stderr) or STILES_ERR_INVALID_ARG.
 namespace {
 
@@ -1143,8 +1146,8 @@ PartRect part_rect(const Task& tk, int q) {
 
 class RaceCheck {
  public:
-  RaceCheck(const Plan& p, int64_t lim, const std::vector<std::vector<int32_t>>& preds)
-      : p_(p), lim_(lim), n_((int)p.tasks.size()), words_((n_ + 63) / 64) {
+  RaceCheck(const Plan& p, int64_t lim, const std::vector<std::vector<int32_t>>& preds, bool serve)
+      : p_(p), lim_(lim), n_((int)p.tasks.size()), words_((n_ + 63) / 64), serve_(serve) {
     anc_.assign((size_t)n_ * words_, 0ull);
     for (int t = 0; t < n_; ++t)
       for (int32_t q : preds[t]) {
@@ -1162,6 +1165,7 @@ class RaceCheck {
 
   // one access of part `id` (4 task + part) to element `off` of buffer `buf`
   bool access(int buf, int64_t off, int id, bool write) {
+    if (serve_ && buf == BUF_A) buf = BUF_L;  // a served request's A is built in place in L
     if (buf < 0 || buf > 3 || off < 0 || off >= lim_) return fail("access outside the buffers", id, -1, buf, off);
     const int t = id >> 2;
     const int w = lw_[buf][off];
@@ -1201,6 +1205,11 @@ class RaceCheck {
     const Task& tk = p_.tasks[t];
     const int id = 4 * t + q;
     if (tk.op == OP_ZERO) return rect(tk.out, tk.ldo, -tk.zrows, tk.zrows, 0, tk.n, id, true);
+    if (tk.op == OP_PREP) {  // the tile column of L (its base-value reads are outside the launch's buffers)
+      const int64_t b = tk.ldo, a = tk.ldc;
+      const int64_t len = (tk.flags & TF_CORNER) ? a * a : (1 + (int64_t)tk.zrows) * b * b + a * b;
+      return len > 0 ? rect(tk.out, (int)len, 0, (int)len, 0, 1, id, true) : true;
+    }
     const PartRect x = part_rect(tk, q);
     if (x.rm <= 0 || x.cn <= 0) return true;
     for (int g = tk.seg0; g < tk.seg0 + tk.nseg; ++g) {
@@ -1237,6 +1246,7 @@ class RaceCheck {
   const Plan& p_;
   int64_t lim_;
   int n_, words_;
+  bool serve_;
   std::vector<uint64_t> anc_;
   std::vector<int> lw_[4], head_[4];
   std::vector<std::pair<int, int>> pool_;
@@ -1244,7 +1254,7 @@ class RaceCheck {
 
 }  // namespace
 
-int race_check_plan(const Plan& p, int64_t lim, int plant) {
+int race_check_plan(const Plan& p, int64_t lim, int plant, bool serve) {
   const int n = (int)p.tasks.size();
   if (n > 16384 || (int64_t)p.succ_off.size() != (int64_t)n + 1) return STILES_ERR_INVALID_ARG;
   std::vector<std::vector<int32_t>> preds(n);
@@ -1262,8 +1272,8 @@ int race_check_plan(const Plan& p, int64_t lim, int plant) {
     preds[victim].clear();
   }
   for (const Task& tk : p.tasks)
-    if (tk.op == OP_PREP) return STILES_ERR_INVALID_ARG;  // request-server tables are not modelled
-  RaceCheck rc(p, lim, preds);
+    if (tk.op == OP_PREP && !serve) return STILES_ERR_INVALID_ARG;
+  RaceCheck rc(p, lim, preds, serve);
   for (int t = 0; t < n; ++t)
     for (int q = 0; q < std::max(1, (int)p.tasks[t].parts); ++q)
       if (!rc.task_part(t, q)) return STILES_ERR_PLAN;

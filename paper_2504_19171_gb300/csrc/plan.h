@@ -216,7 +216,7 @@ int validate_plan(const Plan& p, const Shape& s, int kind);
 // the scratch's packed part), for batch plans.
 int validate_plan_len(const Plan& p, int64_t buf_doubles, int kind);
 // Host race check of a plan (see plan.cpp); plant = 1 plants a race first.
-int race_check_plan(const Plan& p, int64_t buf_doubles, int plant);
+int race_check_plan(const Plan& p, int64_t buf_doubles, int plant, bool serve = false);
 
 // Fused task table of one shape for the request server: as the fused plan,
 // plus one OP_PREP task per tile column that writes the request's A (in the

@@ -473,6 +473,16 @@ extern "C" int stiles_debug_race_check(int nt, int b, int band, int arrow, int w
   return rc ? rc : race_check_plan(p, Layout(sh).doubles(), plant);
 }
 
+extern "C" int stiles_debug_race_check_serve(int nt, int b, int band, int arrow, int precision, int tuning, int plant) {
+  if (nt < 1 || b < 1 || band < 0 || arrow < 0 || precision < 0 || precision > PREC_FP32X || !tune_valid(tuning) ||
+      plant < 0 || plant > 1)
+    return STILES_ERR_INVALID_ARG;
+  const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, precision, tuning};
+  Plan p;
+  const int rc = build_serve_template(sh, 304, &p);
+  return rc ? rc : race_check_plan(p, Layout(sh).doubles(), plant, true);
+}
+
 extern "C" int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, int mode) {
   if (which < 0 || which > 2 || nt < 1 || b < 1 || band < 0 || arrow < 0) return STILES_ERR_INVALID_ARG;
   Plan p;

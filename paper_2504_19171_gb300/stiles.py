@@ -54,7 +54,7 @@ EXPORTS = [
     "stiles_server_submit", "stiles_server_poll", "stiles_server_result", "stiles_server_sigma",
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
     "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status", "stiles_server_submit_values",
-    "stiles_debug_occupancy", "stiles_debug_race_check",
+    "stiles_debug_occupancy", "stiles_debug_race_check", "stiles_debug_race_check_serve",
 ]
 
 
@@ -83,6 +83,7 @@ def _load() -> ctypes.CDLL:
         "stiles_plan_stats": [i32, i32, i32, i32, i32, i32, P(i64)],
         "stiles_debug_check_corrupted": [i32, i32, i32, i32, i32, i32],
         "stiles_debug_race_check": [i32, i32, i32, i32, i32, i32],
+        "stiles_debug_race_check_serve": [i32, i32, i32, i32, i32, i32, i32],
         "stiles_debug_break_plan": [vp, i32],
         "stiles_destroy": [vp],
         "stiles_strerror": [i32],
@@ -228,6 +229,12 @@ def stiles_debug_race_check(nt: int, b: int, band: int, arrow: int, which: int, 
                             plant: int = 0) -> int:
     """Host race check of a plan (0 = race-free; see include/stiles.h)."""
     return _lib.stiles_debug_race_check(nt, b, band, arrow, which + 16 * precision, plant)
+
+
+def stiles_debug_race_check_serve(nt: int, b: int, band: int, arrow: int, precision: int = STILES_FP64,
+                                  tuning: int = 0, plant: int = 0) -> int:
+    """Host race check of a request-server template (0 = race-free)."""
+    return _lib.stiles_debug_race_check_serve(nt, b, band, arrow, precision, tuning, plant)
 
 
 def stiles_debug_check_corrupted(nt: int, b: int, band: int, arrow: int, which: int, mode: int) -> int:

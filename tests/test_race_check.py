@@ -44,3 +44,16 @@ def test_planted_race_is_found(shape):
 def test_bad_arguments():
     assert S.stiles_debug_race_check(4, 64, 1, 0, S.PLAN_FUSED, plant=2) == S.STILES_ERR_INVALID_ARG
     assert S.stiles_debug_race_check(0, 64, 1, 0, S.PLAN_FUSED) == S.STILES_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", [(6, 128, 2, 24), (4, 192, 1, 40), (3, 100, 2, 37), (2, 64, 1, 0)])
+@pytest.mark.parametrize("precision", [S.STILES_FP64, S.STILES_EMU64])
+def test_serve_templates_race_free(shape, precision):
+    """Request-server templates: the request's A is built in place in L by
+    PREP tasks; every task touching a tile column of L (including the tasks
+    that zero L's strict upper part) must come after that column's PREP."""
+    assert S.stiles_debug_race_check_serve(*shape, precision) == S.STILES_OK
+
+
+def test_serve_template_planted_race_is_found():
+    assert S.stiles_debug_race_check_serve(4, 192, 1, 40, plant=1) == S.STILES_ERR_PLAN
