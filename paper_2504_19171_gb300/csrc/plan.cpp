@@ -1171,7 +1171,8 @@ class RaceCheck {
     const int w = lw_[buf][off];
     if (w >= 0 && w != id && !before(w >> 2, t)) return fail(write ? "unordered writes" : "read not ordered after the write", w, id, buf, off);
     if (!write) {
-      // keep the readers since the last write that no later reader descends from
+      // readers since the last write; one the new reader descends from is dropped
+      // (a writer ordered after the new reader is ordered after it too)
       int* link = &head_[buf][off];
       while (*link >= 0) {
         const int r = pool_[*link].first;

@@ -552,7 +552,7 @@ __device__ __forceinline__ void accumulate(const KParams& p, const Task& tk, con
 // uses S = 8 digits of DB = 8 bits (|X| < 2^62: entries down to 2^-9 of their
 // row maximum keep all 53 bits, the dropped levels weigh below 2^-56 of the
 // leading product). The FP32-class mode uses no shared exponent: every entry
-// becomes its FP32 value (rounded toward zero) written as three bf16 pieces
+// becomes its FP32 value (rounded to nearest) written as three bf16 pieces
 // that keep their own exponents (piece_pairs), in the same four-plane layout
 // with a zero fourth plane; its cells hold ordinary FP32 sums.
 //
@@ -680,27 +680,18 @@ __device__ __forceinline__ void digit_pairs(double v0, double v1, int emax, uint
   // in unsigned arithmetic: with DB S = 64 the bias C is above 2^63
   const unsigned long long y0 = (unsigned long long)fixed_point<BITS>(v0, emax) + C;
   const unsigned long long y1 = (unsigned long long)fixed_point<BITS>(v1, emax) + C;
-  if constexpr (DB == 8) {
-    // digit t is byte S - 1 - t of y: one byte permute puts it under the
-    // exponent of 2^23 (bytes 0x00, 0x00, 0x4B above it)
-    const uint32_t h0[2] = {(uint32_t)y0, (uint32_t)(y0 >> 32)}, h1[2] = {(uint32_t)y1, (uint32_t)(y1 >> 32)};
+  static_assert(DB == 8 && S <= 8, "byte digits of a 64-bit value");
+  // digit t is byte S - 1 - t of y: one byte permute puts it under the
+  // exponent of 2^23 (bytes 0x00, 0x00, 0x4B above it); the float minus
+  // 2^23 + 2^(DB-1) is the digit exactly, and its bf16 is its upper half
+  const uint32_t h0[2] = {(uint32_t)y0, (uint32_t)(y0 >> 32)}, h1[2] = {(uint32_t)y1, (uint32_t)(y1 >> 32)};
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-      const int bi = S - 1 - t;
-      const uint32_t sel = 0x7540u | (uint32_t)(bi & 3);
-      const float f0 = __uint_as_float(__byte_perm(h0[bi >> 2], 0x4B000000u, sel)) - kMagic;
-      const float f1 = __uint_as_float(__byte_perm(h1[bi >> 2], 0x4B000000u, sel)) - kMagic;
-      w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-    }
-  } else {
-#pragma unroll
-    for (int t = 0; t < S; ++t) {
-      const int s = DB * (S - 1 - t);
-      // exact float of (field - 2^(DB-1)): 2^23 + field, minus 2^23 + 2^(DB-1); its bf16 is its upper half
-      const float f0 = __uint_as_float(0x4B000000u | (unsigned)((y0 >> s) & ((1u << DB) - 1))) - kMagic;
-      const float f1 = __uint_as_float(0x4B000000u | (unsigned)((y1 >> s) & ((1u << DB) - 1))) - kMagic;
-      w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-    }
+  for (int t = 0; t < S; ++t) {
+    const int bi = S - 1 - t;
+    const uint32_t sel = 0x7540u | (uint32_t)(bi & 3);
+    const float f0 = __uint_as_float(__byte_perm(h0[bi >> 2], 0x4B000000u, sel)) - kMagic;
+    const float f1 = __uint_as_float(__byte_perm(h1[bi >> 2], 0x4B000000u, sel)) - kMagic;
+    w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
   }
 }
 
