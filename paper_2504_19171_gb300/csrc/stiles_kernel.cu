@@ -823,8 +823,13 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
   // the part's result, row lane, column 4 js + warp owned by thread (warp, lane)
   double* R = reinterpret_cast<double*>(stage + TC_RES_OFF);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // exponents of the rows of op(A) and columns of op(B) over all segments
-  if constexpr (!FLT) {
+  // A part whose whole K is two stages (one segment of at most 2 TC_KS: the
+  // factor's one-block-column updates) takes the exact row / column exponents
+  // from the two stages' values in registers (in the segment loop below),
+  // read back to back, instead of a pass of its own.
+  bool small = false;
+  if constexpr (!FLT) small = tk.nseg == 1 && load_seg(p, tk.seg0).k <= 2 * TC_KS;
+  if constexpr (!FLT) if (!small) {
     if (tid < 64) rexp[tid] = 0;
     __syncthreads();
     for (int s = 0; s < tk.nseg; ++s) {
@@ -847,6 +852,37 @@ __device__ void accumulate_tc(const KParams& p, const Task& tk, const Sub& sb, d
     const double* B = resolve(p, gs.b) + (tb ? (int64_t)sb.c0 : (int64_t)sb.c0 * gs.ldb);
     double na[8], nb[8];  // the next stage's values, in flight
     tc_load(A, B, gs, sb, 0, na, nb);
+    if (small) {
+      // this thread holds row 8 warp + lane % 8 of op(A) and column 8 warp +
+      // lane % 8 of op(B) at 8 of each stage's K; lanes lane % 8 + 8 m hold the
+      // rest. The second stage is read here for its exponents only (the loop
+      // reads it again as its prefetch, from L2).
+      int ea = 0, eb = 0;
+      if (gs.k > TC_KS) {
+        double xa[8], xb[8];
+        tc_load(A, B, gs, sb, TC_KS, xa, xb);
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+          ea = max(ea, biased_exp(xa[x]));
+          eb = max(eb, biased_exp(xb[x]));
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        ea = max(ea, biased_exp(na[x]));
+        eb = max(eb, biased_exp(nb[x]));
+      }
+#pragma unroll
+      for (int o = 8; o < 32; o <<= 1) {
+        ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, o));
+        eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+      }
+      if (lane < 8) {
+        rexp[8 * warp + lane] = ea;
+        cexp[8 * warp + lane] = eb;
+      }
+      __syncthreads();
+    }
     for (int k0 = 0; k0 < gs.k; k0 += TC_KS) {
       double ca[8], cb[8];
 #pragma unroll
