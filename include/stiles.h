@@ -327,6 +327,14 @@ int stiles_debug_race_check(int nt, int b, int band, int arrow, int which, int p
  * STILES_ERR_INVALID_ARG. Host only; small shapes. */
 int stiles_debug_race_check_serve(int nt, int b, int band, int arrow, int precision, int tuning, int plant);
 
+/* Test hook: the same race check for the merged table of a batch (shapes
+ * and tuning codes as in stiles_debug_validate_batch; each matrix at its own
+ * offset in the shared buffers): conflicts inside a matrix and across
+ * matrices (an offset that lets two matrices overlap) are both reported.
+ * plant as in stiles_debug_race_check. Host only; small batches. */
+int stiles_debug_race_check_batch(int count, const int *nt, const int *b, const int *band, const int *arrow,
+                                  int precision, const int *tuning, int plant);
+
 /* Test hook: make the handle's plan `which` unsatisfiable on the device (one
  * task waits for one more predecessor than it has) without the host check,
  * so that a launch must end with STILES_ERR_TIMEOUT once the wait budget

@@ -934,6 +934,26 @@ extern "C" int stiles_debug_validate_batch(int count, const int* nt, const int* 
   return rc ? rc : validate_plan_len(p, off, PLAN_FUSED);
 }
 
+extern "C" int stiles_debug_race_check_batch(int count, const int* nt, const int* b, const int* band, const int* arrow,
+                                             int precision, const int* tuning, int plant) {
+  if (count < 1 || !nt || !b || !band || !arrow || precision < 0 || precision > PREC_FP32X || plant < 0 || plant > 1)
+    return STILES_ERR_INVALID_ARG;
+  std::vector<Shape> shapes;
+  std::vector<int64_t> base;
+  int64_t off = 0;
+  for (int m = 0; m < count; ++m) {
+    const int tune = tuning ? tuning[m] : 0;
+    if (nt[m] < 1 || b[m] < 1 || band[m] < 0 || arrow[m] < 0 || !tune_valid(tune)) return STILES_ERR_INVALID_ARG;
+    shapes.push_back(Shape{nt[m], b[m], band[m] < nt[m] - 1 ? band[m] : nt[m] - 1, arrow[m], precision, tune});
+    base.push_back(off);
+    off = (int64_t)align_up((size_t)(off + Layout(shapes.back()).doubles()), 32);
+  }
+  Plan p;
+  std::vector<int32_t> diag_base;
+  const int rc = build_batch_plan(shapes, base, 304, &p, &diag_base);
+  return rc ? rc : race_check_plan(p, off, plant);
+}
+
 extern "C" int stiles_debug_validate_serve(int nt, int b, int band, int arrow, int precision, int tuning) {
   if (nt < 1 || b < 1 || band < 0 || arrow < 0 || precision < 0 || precision > PREC_FP32X || !tune_valid(tuning))
     return STILES_ERR_INVALID_ARG;

@@ -55,6 +55,7 @@ EXPORTS = [
     "stiles_server_release", "stiles_server_request_bytes", "stiles_server_stop", "stiles_server_destroy",
     "stiles_debug_validate_serve", "stiles_create_selected", "stiles_server_status", "stiles_server_submit_values",
     "stiles_debug_occupancy", "stiles_debug_race_check", "stiles_debug_race_check_serve",
+    "stiles_debug_race_check_batch",
 ]
 
 
@@ -119,6 +120,7 @@ def _load() -> ctypes.CDLL:
         "stiles_batch_stats": [vp, P(i64)],
         "stiles_batch_destroy": [vp],
         "stiles_debug_validate_batch": [i32, P(i32), P(i32), P(i32), P(i32), i32, P(i32)],
+        "stiles_debug_race_check_batch": [i32, P(i32), P(i32), P(i32), P(i32), i32, P(i32), i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -334,6 +336,14 @@ def stiles_debug_validate_batch(shapes, precision: int = STILES_FP64, tuning=Non
     cols = list(zip(*shapes))
     return _lib.stiles_debug_validate_batch(len(shapes), _ivec(cols[0]), _ivec(cols[1]), _ivec(cols[2]),
                                             _ivec(cols[3]), precision, _ivec(tuning) if tuning is not None else None)
+
+
+def stiles_debug_race_check_batch(shapes, precision: int = STILES_FP64, tuning=None, plant: int = 0) -> int:
+    """Host race check of a batch's merged table (0 = race-free)."""
+    cols = list(zip(*shapes))
+    return _lib.stiles_debug_race_check_batch(len(shapes), _ivec(cols[0]), _ivec(cols[1]), _ivec(cols[2]),
+                                              _ivec(cols[3]), precision,
+                                              _ivec(tuning) if tuning is not None else None, plant)
 
 
 # --------------------------------------------------------- layout -----

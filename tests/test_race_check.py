@@ -57,3 +57,17 @@ def test_serve_templates_race_free(shape, precision):
 
 def test_serve_template_planted_race_is_found():
     assert S.stiles_debug_race_check_serve(4, 192, 1, 40, plant=1) == S.STILES_ERR_PLAN
+
+
+@pytest.mark.parametrize("precision", [S.STILES_FP64, S.STILES_EMU64, S.STILES_FP32X])
+def test_batch_tables_race_free(precision):
+    """Merged batch tables: every matrix's tasks at its own offsets; no
+    conflict inside a matrix or across matrices, with per-matrix tuning codes."""
+    shapes = [(3, 128, 1, 16), (4, 64, 2, 0), (2, 192, 1, 40), (5, 96, 3, 7)]
+    assert S.stiles_debug_race_check_batch(shapes, precision) == S.STILES_OK
+    assert S.stiles_debug_race_check_batch(shapes, precision, tuning=[0, 4 + 16, 2 + 8, 1]) == S.STILES_OK
+
+
+def test_batch_planted_race_is_found():
+    shapes = [(3, 128, 1, 16), (2, 192, 1, 40)]
+    assert S.stiles_debug_race_check_batch(shapes, plant=1) == S.STILES_ERR_PLAN
