@@ -161,6 +161,7 @@ struct Builder {
   std::vector<int64_t> lctr_base;  // per (i,k) tile: first index into lctr, or -1
   std::vector<int32_t> lfinal;     // per L block: number of writers (updates + final)
   std::vector<int32_t> colfinal;   // fused: per tile column, counter of "L column final"
+  std::vector<int32_t> coljoin;    // fused: per tile column, the join task's counter (one writer)
   std::vector<int32_t> colblocks;  // fused: number of L blocks per tile column
 
   int tile_slot(int i, int k) const {  // 0 = diag, 1..w = band, w+1 = arrow
@@ -527,6 +528,16 @@ struct Builder {
     // Sigma of tile column i depends only on Sigma of the columns after it and
     // on column i's own phase 1: a selection starting at column sel0 needs
     // exactly the phase-1 and phase-2 work of columns >= sel0.
+    if (kind == PLAN_FUSED) {
+      // one join per tile column waits for all of its L blocks; the column's
+      // phase-1 tasks wait for the join (one dependency each instead of one
+      // per L block: a column of ~400 blocks and ~400 phase-1 tasks)
+      coljoin.assign(cols, -1);
+      for (int i = s.sel0; i < cols; ++i) {
+        coljoin[i] = newctr(true);
+        emit(blank(OP_JOIN, 0, 0), {}, {{colfinal[i], colblocks[i]}}, {coljoin[i]}, 0.0);
+      }
+    }
     for (int i = s.sel0; i < cols; ++i) emit_phase1(i);
     for (int i = cols - 1; i >= s.sel0; --i) emit_phase2(i);
   }
@@ -538,7 +549,7 @@ struct Builder {
   int32_t scol(int j, int i, int c) const { return s_col[st_cbase[slot_index(j, i)] + c]; }
 
   void add_fused_wait(int i, std::vector<Wait>& w) {
-    if (kind == PLAN_FUSED) w.push_back({colfinal[i], colblocks[i]});
+    if (kind == PLAN_FUSED) w.push_back({coljoin[i], 1});
   }
 
   void emit_phase1(int i) {
@@ -941,7 +952,7 @@ int check_plan(const Plan& p) {
     if (tk.wait0 < 0 || tk.nwait < 0 || (int64_t)tk.wait0 + tk.nwait > (int64_t)p.waits.size()) return STILES_ERR_PLAN;
     if (tk.seg0 < 0 || tk.nseg < 0 || (int64_t)tk.seg0 + tk.nseg > (int64_t)p.segs.size()) return STILES_ERR_PLAN;
     if (tk.sig0 < 0 || tk.nsig < 0 || (int64_t)tk.sig0 + tk.nsig > (int64_t)p.sigs.size()) return STILES_ERR_PLAN;
-    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_ZERO) return STILES_ERR_PLAN;
+    if (tk.m < 0 || tk.n < 0 || tk.m > FB || tk.n > FB || tk.op > OP_JOIN) return STILES_ERR_PLAN;
     if (tk.parts < 1 || tk.parts > 4 || tk.pmode > PM_QUAD16 || tk.prec > PREC_FP32X) return STILES_ERR_PLAN;
     for (int q = 0; q < tk.nwait; ++q) {
       const Wait& w = p.waits[tk.wait0 + q];
@@ -996,6 +1007,10 @@ int validate_plan_len(const Plan& p, int64_t lim, int kind) {
           !in_base(tk.aux, 0, rows - 1) || !in_base(tk.aux, tk.gcol, tk.gcol + rows - 1) ||
           (int64_t)tk.diag + rows > (int64_t)tk.gcol)
         return bad("PREP out of bounds", t);
+      continue;
+    }
+    if (tk.op == OP_JOIN) {  // no work, no access
+      if (tk.parts != 1 || tk.nseg != 0) return bad("join with work", t);
       continue;
     }
     if (tk.op == OP_ZERO) {  // zrows x n above the block
@@ -1205,6 +1220,7 @@ class RaceCheck {
   bool task_part(int t, int q) {
     const Task& tk = p_.tasks[t];
     const int id = 4 * t + q;
+    if (tk.op == OP_JOIN) return true;
     if (tk.op == OP_ZERO) return rect(tk.out, tk.ldo, -tk.zrows, tk.zrows, 0, tk.n, id, true);
     if (tk.op == OP_PREP) {  // the tile column of L (its base-value reads are outside the launch's buffers)
       const int64_t b = tk.ldo, a = tk.ldc;

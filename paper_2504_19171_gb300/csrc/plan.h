@@ -41,6 +41,7 @@ enum Op : uint8_t {
                     // diagonal tau + rho rb[i] + ra[i] (rb / ra = band / arrow absolute row sums)
   OP_ZERO = 9,      // the zrows x n block above out (L's strict upper part in a diagonal tile's
                     // block column) set to zero; off the factorization's critical path
+  OP_JOIN = 10,     // no work: one dependency point for many waiters (a tile column of L final)
 };
 
 // How a task's output block is divided among CTAs (each part runs as its own

@@ -1547,6 +1547,7 @@ __device__ void run_task(const KParams& p, const Task& tk, int t, int q, double*
     run_zero(p, tk, t);
     return;
   }
+  if (tk.op == OP_JOIN) return;  // a dependency point only
   const Sub sb = sub_of(tk, q);
   if (sb.rm <= 0 || sb.cn <= 0) return;
 #ifdef STILES_CHECKED

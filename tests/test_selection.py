@@ -67,8 +67,10 @@ def test_update_runs_only_in_full_fused_plans():
     """The planner merges far one-block-column update terms into runs only in
     a fused plan of every column: that plan has fewer tasks than the factor
     and selected-inversion plans together, while a column-selected fused plan
-    has exactly their sum (single terms). Every one of these plans validates
-    (satisfiable waits, in-bounds accesses)."""
+    has exactly their sum (single terms) plus one join task per selected column
+    of L (tile columns first .. nt-1 and the arrow column: the point where that
+    column of L is final). Every one of these plans validates (satisfiable
+    waits, in-bounds accesses)."""
     from paper_2504_19171_gb300 import stiles as S
     for shape in [(3, 640, 1, 16), (4, 576, 2, 9), (2, 1024, 1, 8)]:
         fac = S.stiles_plan_stats(*shape, S.PLAN_FACTOR)["tasks"]
@@ -80,5 +82,5 @@ def test_update_runs_only_in_full_fused_plans():
             which = first << 16
             f = S.stiles_plan_stats(*shape, S.PLAN_FUSED + which)["tasks"]
             s = S.stiles_plan_stats(*shape, S.PLAN_SELINV + which)["tasks"]
-            assert f == fac + s, (shape, first)
+            assert f == fac + s + (shape[0] + 1 - first), (shape, first)
             assert S.stiles_debug_validate(*shape, S.PLAN_FUSED + which) == S.STILES_OK, (shape, first)
