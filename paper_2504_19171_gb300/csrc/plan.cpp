@@ -52,12 +52,13 @@ struct Builder {
   // per emitted task (emission order is topological)
   std::vector<Task> tasks;
   std::vector<double> cost;
-  std::vector<std::vector<Seg>> tsegs;
-  std::vector<std::vector<Wait>> twaits;
-  std::vector<std::vector<int32_t>> tsigs;
-  // counters
-  std::vector<char> chain;                    // 1: writers strictly ordered
-  std::vector<std::vector<int32_t>> writers;  // emission ids in signal order
+  // segments, waits and signalled counters of task t: [off[t], off[t+1]) of each flat array
+  std::vector<Seg> fsegs;
+  std::vector<Wait> fwaits;
+  std::vector<int32_t> fsigs;
+  std::vector<int64_t> seg_off{0}, wait_off{0}, sig_off{0};
+  // counters (their writers, in emission order, are the tasks that list them in fsigs)
+  std::vector<char> chain;  // 1: writers strictly ordered
   double flops = 0;
   double flops_lowered = 0;  // algorithmic flops of the reduced-precision block products
   bool sym_block = false;    // the next emitted task updates a symmetric diagonal block (m^2 k per term)
@@ -71,7 +72,6 @@ struct Builder {
 
   int32_t newctr(bool is_chain) {
     chain.push_back(is_chain ? 1 : 0);
-    writers.emplace_back();
     return (int32_t)chain.size() - 1;
   }
 
@@ -90,10 +90,12 @@ struct Builder {
     // parts run side by side on different CTAs
     cost.push_back(kTaskOverheadNs + f / kFlopPerNs / t.parts +
                    epi_ns / (t.pmode == PM_ROWS2 ? 2 : t.pmode == PM_ROWS4 ? 4 : 1));
-    tsegs.push_back(std::move(segs));
-    twaits.push_back(std::move(waits));
-    for (int32_t c : sigs) writers[c].push_back(id);
-    tsigs.push_back(std::move(sigs));
+    fsegs.insert(fsegs.end(), segs.begin(), segs.end());
+    seg_off.push_back((int64_t)fsegs.size());
+    fwaits.insert(fwaits.end(), waits.begin(), waits.end());
+    wait_off.push_back((int64_t)fwaits.size());
+    fsigs.insert(fsigs.end(), sigs.begin(), sigs.end());
+    sig_off.push_back((int64_t)fsigs.size());
     return id;
   }
 
@@ -691,46 +693,89 @@ struct Builder {
   // ---------------------------------------------------------- schedule ----
   int finish(int workers) {
     const int nt_ = (int)tasks.size();
-    // predecessor edges from waits
-    std::vector<std::vector<int32_t>> succ(nt_);
-    std::vector<int32_t> indeg(nt_, 0);
+    // predecessor edges from waits (flat, per task sorted and unique); the
+    // emission order must be topological
+    // writers of each counter, in emission order
+    const int64_t nctr = (int64_t)chain.size();
+    std::vector<int64_t> woff(nctr + 1, 0);
+    for (int32_t c : fsigs) {
+      if (c < 0 || c >= nctr) return STILES_ERR_PLAN;
+      woff[c + 1]++;
+    }
+    for (int64_t c = 0; c < nctr; ++c) woff[c + 1] += woff[c];
+    std::vector<int32_t> wr(fsigs.size());
+    {
+      std::vector<int64_t> fill(woff.begin(), woff.end() - 1);
+      for (int t = 0; t < nt_; ++t)
+        for (int64_t e = sig_off[t]; e < sig_off[t + 1]; ++e) wr[fill[fsigs[e]]++] = t;
+    }
+    std::vector<int64_t> poff(nt_ + 1, 0);
+    std::vector<int32_t> pred;
+    pred.reserve(fwaits.size() + fwaits.size() / 2);
+    std::vector<int32_t> scratch;
     for (int t = 0; t < nt_; ++t) {
-      std::vector<int32_t> preds;
-      for (const Wait& w : twaits[t]) {
-        const auto& wr = writers[w.ctr];
-        if (w.need > (int)wr.size() || w.need < 0) return STILES_ERR_PLAN;
+      scratch.clear();
+      for (int64_t e = wait_off[t]; e < wait_off[t + 1]; ++e) {
+        const Wait& w = fwaits[e];
+        if (w.ctr < 0 || w.ctr >= nctr) return STILES_ERR_PLAN;
+        const int64_t w0 = woff[w.ctr], nw = woff[w.ctr + 1] - w0;
+        if (w.need > nw || w.need < 0) return STILES_ERR_PLAN;
         if (w.need == 0) continue;
-        if (chain[w.ctr]) preds.push_back(wr[w.need - 1]);
-        else for (int q = 0; q < w.need; ++q) preds.push_back(wr[q]);
+        if (chain[w.ctr]) scratch.push_back(wr[w0 + w.need - 1]);
+        else scratch.insert(scratch.end(), wr.begin() + w0, wr.begin() + w0 + w.need);
       }
-      std::sort(preds.begin(), preds.end());
-      preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
-      for (int32_t p : preds) {
-        if (p >= t) return STILES_ERR_PLAN;  // emission order must be topological
-        succ[p].push_back(t);
-        indeg[t]++;
+      std::sort(scratch.begin(), scratch.end());
+      scratch.erase(std::unique(scratch.begin(), scratch.end()), scratch.end());
+      if (!scratch.empty() && scratch.back() >= t) return STILES_ERR_PLAN;
+      pred.insert(pred.end(), scratch.begin(), scratch.end());
+      poff[t + 1] = (int64_t)pred.size();
+    }
+    if (pred.size() > (size_t)INT32_MAX) return STILES_ERR_PLAN;
+    // successors of each task, in ascending task order
+    std::vector<int64_t> soff(nt_ + 1, 0);
+    for (int32_t q : pred) soff[q + 1]++;
+    for (int t = 0; t < nt_; ++t) soff[t + 1] += soff[t];
+    std::vector<int32_t> succ(pred.size());
+    std::vector<int32_t> indeg(nt_, 0);
+    {
+      std::vector<int64_t> fill(soff.begin(), soff.end() - 1);
+      for (int t = 0; t < nt_; ++t) {
+        indeg[t] = (int32_t)(poff[t + 1] - poff[t]);
+        for (int64_t e = poff[t]; e < poff[t + 1]; ++e) succ[fill[pred[e]]++] = t;
       }
     }
+    std::vector<int32_t>().swap(pred);
+    std::vector<int64_t>().swap(poff);
+    std::vector<int32_t>().swap(wr);
+    std::vector<int64_t>().swap(woff);
     // bottom levels
     std::vector<double> blevel(nt_, 0.0);
     double cp = 0;
     for (int t = nt_ - 1; t >= 0; --t) {
       double best = 0;
-      for (int32_t q : succ[t]) best = std::max(best, blevel[q]);
+      for (int64_t e = soff[t]; e < soff[t + 1]; ++e) best = std::max(best, blevel[succ[e]]);
       blevel[t] = cost[t] + best;
       cp = std::max(cp, blevel[t]);
     }
     // list schedule: free workers take the ready task with the largest bottom level
     using RItem = std::pair<double, int32_t>;
-    std::priority_queue<RItem> ready;
     using EItem = std::pair<double, int32_t>;  // (finish time, task)
-    std::priority_queue<EItem, std::vector<EItem>, std::greater<EItem>> running;
+    std::vector<RItem> rbuf;
+    rbuf.reserve(nt_);
+    std::priority_queue<RItem> ready(std::less<RItem>(), std::move(rbuf));
+    std::vector<EItem> ebuf;
+    ebuf.reserve((size_t)std::max(1, workers) + 1);
+    std::priority_queue<EItem, std::vector<EItem>, std::greater<EItem>> running(std::greater<EItem>(), std::move(ebuf));
     for (int t = 0; t < nt_; ++t)
       if (indeg[t] == 0) ready.push({blevel[t], t});
     std::vector<int32_t> order;
     order.reserve(nt_);
     double now = 0;
     int free_workers = std::max(1, workers);
+    auto release = [&](int32_t t) {
+      for (int64_t e = soff[t]; e < soff[t + 1]; ++e)
+        if (--indeg[succ[e]] == 0) ready.push({blevel[succ[e]], succ[e]});
+    };
     while ((int)order.size() < nt_) {
       while (free_workers > 0 && !ready.empty()) {
         int32_t t = ready.top().second;
@@ -744,46 +789,45 @@ struct Builder {
       running.pop();
       now = e.first;
       ++free_workers;
-      for (int32_t q : succ[e.second])
-        if (--indeg[q] == 0) ready.push({blevel[q], q});
+      release(e.second);
       while (!running.empty() && running.top().first <= now) {
         EItem e2 = running.top();
         running.pop();
         ++free_workers;
-        for (int32_t q : succ[e2.second])
-          if (--indeg[q] == 0) ready.push({blevel[q], q});
+        release(e2.second);
       }
     }
     while (!running.empty()) { now = std::max(now, running.top().first); running.pop(); }
     // write the plan in list-schedule order (the device queue order)
     Plan& p = *out;
     p.tasks.clear(); p.segs.clear(); p.waits.clear(); p.sigs.clear();
-    p.tasks.reserve(nt_);
+    p.tasks.reserve(nt_); p.segs.reserve(fsegs.size()); p.waits.reserve(fwaits.size()); p.sigs.reserve(fsigs.size());
     std::vector<int32_t> rank(nt_);
     for (int r = 0; r < nt_; ++r) rank[order[r]] = r;
     for (int32_t t : order) {
       Task tk = tasks[t];
       tk.seg0 = (int32_t)p.segs.size();
-      tk.nseg = (int32_t)tsegs[t].size();
-      for (const Seg& g : tsegs[t]) p.segs.push_back(g);
+      tk.nseg = (int32_t)(seg_off[t + 1] - seg_off[t]);
+      p.segs.insert(p.segs.end(), fsegs.begin() + seg_off[t], fsegs.begin() + seg_off[t + 1]);
       tk.wait0 = (int32_t)p.waits.size();
-      tk.nwait = (int32_t)twaits[t].size();
-      for (const Wait& w : twaits[t]) p.waits.push_back(w);
+      tk.nwait = (int32_t)(wait_off[t + 1] - wait_off[t]);
+      p.waits.insert(p.waits.end(), fwaits.begin() + wait_off[t], fwaits.begin() + wait_off[t + 1]);
       tk.sig0 = (int32_t)p.sigs.size();
-      tk.nsig = (int16_t)tsigs[t].size();
-      for (int32_t c : tsigs[t]) p.sigs.push_back(c);
+      tk.nsig = (int16_t)(sig_off[t + 1] - sig_off[t]);
+      p.sigs.insert(p.sigs.end(), fsigs.begin() + sig_off[t], fsigs.begin() + sig_off[t + 1]);
       p.tasks.push_back(tk);
     }
     // successor graph in schedule-order indices
     p.indeg.assign(nt_, 0);
     p.succ_off.assign(nt_ + 1, 0);
     p.succ.clear();
+    p.succ.reserve(succ.size());
     for (int r = 0; r < nt_; ++r) {
       const int32_t t = order[r];
       p.succ_off[r] = (int32_t)p.succ.size();
-      for (int32_t q : succ[t]) {
-        p.succ.push_back(rank[q]);
-        p.indeg[rank[q]]++;
+      for (int64_t e = soff[t]; e < soff[t + 1]; ++e) {
+        p.succ.push_back(rank[succ[e]]);
+        p.indeg[rank[succ[e]]]++;
       }
     }
     p.succ_off[nt_] = (int32_t)p.succ.size();
@@ -907,7 +951,7 @@ int build_batch_plan(const std::vector<Shape>& shapes, const std::vector<int64_t
     Builder B(shapes[m], PLAN_FUSED, nullptr);
     B.build_factor();
     B.build_selinv();
-    const int32_t toff = (int32_t)M.tasks.size(), coff = (int32_t)M.chain.size(), doff = M.ndiag;
+    const int32_t coff = (int32_t)M.chain.size(), doff = M.ndiag;
     const int64_t off = base[m];
     auto shift = [off](int64_t ref) { return ref < 0 ? ref : ref + off; };
     for (size_t t = 0; t < B.tasks.size(); ++t) {
@@ -917,22 +961,24 @@ int build_batch_plan(const std::vector<Shape>& shapes, const std::vector<int64_t
       tk.aux = shift(tk.aux);
       if (tk.diag >= 0) tk.diag += doff;
       M.tasks.push_back(tk);
-      M.cost.push_back(B.cost[t]);
-      for (Seg& g : B.tsegs[t]) {
-        g.a = shift(g.a);
-        g.b = shift(g.b);
-      }
-      M.tsegs.push_back(std::move(B.tsegs[t]));
-      for (Wait& w : B.twaits[t]) w.ctr += coff;
-      M.twaits.push_back(std::move(B.twaits[t]));
-      for (int32_t& c : B.tsigs[t]) c += coff;
-      M.tsigs.push_back(std::move(B.tsigs[t]));
     }
-    for (size_t c = 0; c < B.chain.size(); ++c) {
-      M.chain.push_back(B.chain[c]);
-      for (int32_t& id : B.writers[c]) id += toff;
-      M.writers.push_back(std::move(B.writers[c]));
+    M.cost.insert(M.cost.end(), B.cost.begin(), B.cost.end());
+    for (Seg g : B.fsegs) {
+      g.a = shift(g.a);
+      g.b = shift(g.b);
+      M.fsegs.push_back(g);
     }
+    for (Wait w : B.fwaits) {
+      w.ctr += coff;
+      M.fwaits.push_back(w);
+    }
+    for (int32_t c : B.fsigs) M.fsigs.push_back(c + coff);
+    for (size_t t = 0; t < B.tasks.size(); ++t) {
+      M.seg_off.push_back(M.seg_off.back() + (B.seg_off[t + 1] - B.seg_off[t]));
+      M.wait_off.push_back(M.wait_off.back() + (B.wait_off[t + 1] - B.wait_off[t]));
+      M.sig_off.push_back(M.sig_off.back() + (B.sig_off[t + 1] - B.sig_off[t]));
+    }
+    M.chain.insert(M.chain.end(), B.chain.begin(), B.chain.end());
     M.ndiag += B.ndiag;
     M.tile_gemms += B.tile_gemms;
     M.flops += tile_flops(shapes[m], PLAN_FUSED);

@@ -61,8 +61,10 @@ enum PartMode : uint8_t {
 // Arithmetic of a task's block products (its epilogue is always FP64).
 enum Precision : uint8_t {
   PREC_FP64 = 0,   // FP64 FMA pipe
-  PREC_EMU64 = 1,  // split-precision emulated FP64: 7 bf16 digit planes per operand on the tensor cores
-  PREC_FP32X = 2,  // FP32 FMA pipe (FP32-class)
+  PREC_EMU64 = 1,  // split-precision emulated FP64: 8 fixed-point digits of 8 bits per operand (bf16
+                   // planes) against per-row / per-column exponents, products on the tensor cores
+  PREC_FP32X = 2,  // FP32-class: each operand's FP32 value as three bf16 pieces, products on the
+                   // tensor cores with FP32 sums
 };
 
 // Task flags.

@@ -318,16 +318,23 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
-// Device address of the array on `device` (which must be current). Looked up
-// once per device; the host-side name of the array is not a device address.
-int noalloc_scratch(int device, void** out) {
+// Device address of the array on `device` (which must be current). The
+// host-side name of the array is not a device address. Outside stream capture
+// it is looked up on every call (an address kept from before a device or
+// primary-context reset would be stale) and remembered; a call made while
+// `stream` is capturing uses the address remembered by the last uncaptured
+// call on that device, so no runtime lookup is made during capture.
+int noalloc_scratch(int device, cudaStream_t stream, void** out) {
   if (device < 0 || device >= kMaxDevices) return STILES_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return STILES_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return STILES_ERR_CUDA;
     g_noalloc_ptr[device] = ptr;
   }
+  if (!g_noalloc_ptr[device]) return STILES_ERR_INVALID_ARG;  // first call on this device is being captured
   *out = g_noalloc_ptr[device];
   return STILES_OK;
 }
@@ -338,7 +345,7 @@ extern "C" int stiles_factor_selinv_noalloc(stiles_t h, const double* A, double*
   if (h->scratch_bytes > STILES_NOALLOC_SCRATCH_BYTES) return STILES_ERR_TOO_LARGE;
   if (cudaSetDevice(h->device) != cudaSuccess) return STILES_ERR_CUDA;
   void* scratch = nullptr;
-  const int rc = noalloc_scratch(h->device, &scratch);
+  const int rc = noalloc_scratch(h->device, (cudaStream_t)stream, &scratch);
   if (rc) return rc;
   return launch(h, PLAN_FUSED, A, L, S, scratch, stream);
 }
