@@ -51,11 +51,11 @@ VARIANT_PRODUCTS = {"emu64": {"pipe": "bf16 tensor (tcgen05)", "digits": 8, "pro
                     "fp32x": {"pipe": "bf16 tensor (tcgen05)", "digits": 3, "products": 10}}
 
 # DRAM traffic of the persistent kernel per launch, from ncu captures of the
-# nt = 8 and nt = 16 cases of the same matrix family (0.804 GB and 2.081 GB):
+# nt = 8 and nt = 16 cases of the same matrix family (0.791 GB and 2.086 GB):
 # the nt = 8 figure plus 192 more tile columns at the marginal 8 -> 16 rate.
 # Valid only for the kernel source it was measured on (sha256 prefix of
 # stiles_kernel.cu + plan.cpp); otherwise reported as null.
-TRAFFIC = {"sources_sha": "372d1de158642877", "bytes_per_launch": 31.44e9}
+TRAFFIC = {"sources_sha": "372d1de158642877", "bytes_per_launch": 31.87e9}
 
 
 def measured_peaks() -> dict:
