@@ -279,10 +279,12 @@ int stiles_trace(stiles_t h, unsigned long long *out_host, size_t capacity, size
  *     (the count of the GEMM-count table of Sec. III-E and Appendix A),
  * [6] critical path and [7] list-schedule makespan, in estimated ns,
  * [8] the part of [4] that runs as block products in the plan's reduced
- *     precision (0 for STILES_FP64; the rest stays on the FP64 pipe).
+ *     precision (0 for STILES_FP64; the rest stays on the FP64 pipe),
+ * [9] successor edges of the dependency graph (each costs one device atomic
+ *     when its source task completes).
  * Returns STILES_ERR_INVALID_ARG for a bad shape, STILES_ERR_PLAN if the
  * table fails its consistency check. */
-int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[9]);
+int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[10]);
 
 /* Test hook: CTAs of the persistent kernel that can be resident on one SM of
  * the current device with the shared memory of an FP64 plan (tensor_parts =

@@ -433,7 +433,7 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
   }
 }
 
-extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[9]) {
+extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, int workers, long long stats[10]) {
   const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
   if (!stats || kind < 0 || kind > 2 || prec > PREC_FP32X || workers < 1 || !tune_valid(tune))
     return STILES_ERR_INVALID_ARG;
@@ -451,6 +451,7 @@ extern "C" int stiles_plan_stats(int nt, int b, int band, int arrow, int which, 
   stats[6] = (long long)p.cp_ns;
   stats[7] = (long long)p.makespan_ns;
   stats[8] = (long long)p.flops_lowered;
+  stats[9] = (long long)p.succ.size();
   return STILES_OK;
 }
 

@@ -216,10 +216,10 @@ def stiles_set_option(h: int, option: int, value: int) -> None:
 
 def stiles_plan_stats(nt: int, b: int, band: int, arrow: int, which: int, workers: int = 152,
                       precision: int = STILES_FP64) -> Dict[str, int]:
-    st = (ctypes.c_longlong * 9)()
+    st = (ctypes.c_longlong * 10)()
     _check(_lib.stiles_plan_stats(nt, b, band, arrow, which + 16 * precision, workers, st), "stiles_plan_stats")
     keys = ["tasks", "segments", "waits", "counters", "flops", "tile_gemms", "critical_path_ns", "makespan_ns",
-            "flops_lowered"]
+            "flops_lowered", "edges"]
     return dict(zip(keys, list(st)))
 
 
