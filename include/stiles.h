@@ -314,10 +314,13 @@ int stiles_debug_check_corrupted(int nt, int b, int band, int arrow, int which, 
  * accesses follow the kernel's: operand regions of each segment, the input
  * sub-block, the lower triangle of a triangular block, the output sub-block,
  * SYMUPD's mirror, the rows a ZERO task clears. plant = 1 removes every
- * predecessor of the last POTRF that has some before the check (a planted
- * race, expected to be found). Returns STILES_OK, STILES_ERR_PLAN (the first
- * race printed to stderr) or STILES_ERR_INVALID_ARG (bad arguments, or a
- * plan of more than 16384 tasks). Host only; memory grows with the buffers
+ * predecessor of the last POTRF that has some before the check; plant = 2
+ * removes every edge into the first column-join task of a fused plan (its
+ * tile column's phase 1 then no longer follows that column of L). Both are
+ * planted races, expected to be found. Returns STILES_OK, STILES_ERR_PLAN
+ * (the first race printed to stderr) or STILES_ERR_INVALID_ARG (bad
+ * arguments, plant = 2 on a plan without a join task, or a plan of more
+ * than 16384 tasks). Host only; memory grows with the buffers
  * (12 bytes per element) -- meant for small shapes. */
 int stiles_debug_race_check(int nt, int b, int band, int arrow, int which, int plant);
 

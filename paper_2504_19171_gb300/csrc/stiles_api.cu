@@ -470,15 +470,44 @@ extern "C" int stiles_debug_validate(int nt, int b, int band, int arrow, int whi
   return rc ? rc : validate_plan(p, sh, kind);
 }
 
+// Planted race of the race-check hook (plant = 2): every successor edge into
+// the first column-join task of the table removed, so that the join -- and
+// the phase-1 tasks that wait on it -- no longer follow the L blocks of their
+// tile column. Returns false if the table has no join task.
+static bool plant_unjoined_column(Plan& p) {
+  const int n = (int)p.tasks.size();
+  int join = -1;
+  for (int t = 0; t < n && join < 0; ++t)
+    if (p.tasks[t].op == OP_JOIN) join = t;
+  if (join < 0) return false;
+  std::vector<int32_t> off(n + 1, 0), succ;
+  succ.reserve(p.succ.size());
+  for (int t = 0; t < n; ++t) {
+    off[t] = (int32_t)succ.size();
+    for (int e = p.succ_off[t]; e < p.succ_off[t + 1]; ++e)
+      if (p.succ[e] != join) succ.push_back(p.succ[e]);
+  }
+  off[n] = (int32_t)succ.size();
+  p.succ_off.swap(off);
+  p.succ.swap(succ);
+  p.indeg[join] = 0;
+  return true;
+}
+
 extern "C" int stiles_debug_race_check(int nt, int b, int band, int arrow, int which, int plant) {
   const int kind = which & 15, prec = (which >> 4) & 15, tune = (which >> 8) & 255, sel0 = which >> 16;
   if (kind < 0 || kind > 2 || prec > PREC_FP32X || !tune_valid(tune) || nt < 1 || b < 1 || band < 0 || arrow < 0 ||
-      plant < 0 || plant > 1)
+      plant < 0 || plant > 2)
     return STILES_ERR_INVALID_ARG;
   const Shape sh{nt, b, band < nt - 1 ? band : nt - 1, arrow, prec, tune, sel0};
   Plan p;
   const int rc = build_plan(sh, (PlanKind)kind, 304, &p);
-  return rc ? rc : race_check_plan(p, Layout(sh).doubles(), plant);
+  if (rc) return rc;
+  if (plant == 2) {
+    if (!plant_unjoined_column(p)) return STILES_ERR_INVALID_ARG;
+    return race_check_plan(p, Layout(sh).doubles(), 0);
+  }
+  return race_check_plan(p, Layout(sh).doubles(), plant);
 }
 
 extern "C" int stiles_debug_race_check_serve(int nt, int b, int band, int arrow, int precision, int tuning, int plant) {

@@ -41,9 +41,23 @@ def test_planted_race_is_found(shape):
         assert S.stiles_debug_race_check(*shape, kind, plant=1) == S.STILES_ERR_PLAN
 
 
+@pytest.mark.parametrize("shape", [(3, 640, 1, 16), (4, 576, 2, 9), (3, 200, 1, 0)])
+@pytest.mark.parametrize("precision", [S.STILES_FP64, S.STILES_EMU64, S.STILES_FP32X])
+def test_column_join_carries_the_phase1_order(shape, precision):
+    """In a fused plan, phase 1 of a tile column follows that column of L only
+    through the column's join task: with the edges into the first join
+    removed, the column's first phase-1 read of L is unordered after its
+    writer, and the check finds it."""
+    assert S.stiles_debug_race_check(*shape, S.PLAN_FUSED, precision=precision) == S.STILES_OK
+    assert S.stiles_debug_race_check(*shape, S.PLAN_FUSED, precision=precision, plant=2) == S.STILES_ERR_PLAN
+
+
 def test_bad_arguments():
-    assert S.stiles_debug_race_check(4, 64, 1, 0, S.PLAN_FUSED, plant=2) == S.STILES_ERR_INVALID_ARG
+    assert S.stiles_debug_race_check(4, 64, 1, 0, S.PLAN_FUSED, plant=3) == S.STILES_ERR_INVALID_ARG
     assert S.stiles_debug_race_check(0, 64, 1, 0, S.PLAN_FUSED) == S.STILES_ERR_INVALID_ARG
+    # factor and selected-inversion plans have no join task to plant a race in
+    for kind in (S.PLAN_FACTOR, S.PLAN_SELINV):
+        assert S.stiles_debug_race_check(4, 64, 1, 0, kind, plant=2) == S.STILES_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("shape", [(6, 128, 2, 24), (4, 192, 1, 40), (3, 100, 2, 37), (2, 64, 1, 0)])
