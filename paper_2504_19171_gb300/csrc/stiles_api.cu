@@ -52,11 +52,21 @@ std::vector<int32_t> sched_image(const Plan& p) {
   return img;
 }
 
+// cudaMalloc that leaves no error behind when it fails: the failure is
+// reported as STILES_ERR_OOM, and the runtime's last-error slot is cleared so
+// that a later launch check does not pick it up.
+int dev_malloc(void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) == cudaSuccess) return 0;
+  *p = nullptr;
+  cudaGetLastError();
+  return STILES_ERR_OOM;
+}
+
 template <typename T>
 int upload(const std::vector<T>& v, T** out) {
   *out = nullptr;
   if (v.empty()) return 0;
-  if (cudaMalloc((void**)out, v.size() * sizeof(T)) != cudaSuccess) return STILES_ERR_OOM;
+  if (dev_malloc((void**)out, v.size() * sizeof(T))) return STILES_ERR_OOM;
   if (cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return STILES_ERR_CUDA;
   return 0;
 }
@@ -174,9 +184,8 @@ static int create_handle(int nt, int b, int band, int arrow, int precision, int 
     if (img.size() > h->state_ints_max) h->state_ints_max = img.size();
     if (p.ndiag > h->ndiag) h->ndiag = p.ndiag;
   }
-  if (!rc && cudaMalloc((void**)&h->dstatus, 3 * sizeof(DevStatus)) != cudaSuccess) rc = STILES_ERR_OOM;
-  if (!rc && cudaMalloc((void**)&h->dlogdet, sizeof(double) * (h->ndiag > 0 ? h->ndiag : 1)) != cudaSuccess)
-    rc = STILES_ERR_OOM;
+  if (!rc) rc = dev_malloc((void**)&h->dstatus, 3 * sizeof(DevStatus));
+  if (!rc) rc = dev_malloc((void**)&h->dlogdet, sizeof(double) * (h->ndiag > 0 ? h->ndiag : 1));
   if (rc) {
     free_handle(h);
     return rc;
@@ -422,8 +431,7 @@ extern "C" int stiles_set_option(stiles_t h, int option, long long value) {
       if (value) {
         size_t n = 0;
         for (auto& d : h->dev) n = (size_t)d.ntasks > n ? (size_t)d.ntasks : n;
-        if (cudaMalloc((void**)&h->dtrace, 16 * sizeof(unsigned long long) * (n ? n : 1)) != cudaSuccess)
-          return STILES_ERR_OOM;
+        if (dev_malloc((void**)&h->dtrace, 16 * sizeof(unsigned long long) * (n ? n : 1))) return STILES_ERR_OOM;
         h->trace_tasks = n;
       }
       return STILES_OK;
@@ -692,11 +700,9 @@ extern "C" int stiles_batch_create(int count, const int* nt, const int* b, const
   h->dev.nbuckets = p.nbuckets;
   h->dev.ucap = p.urgent_parts;
   h->ndiag = p.ndiag;
-  if (!rc && cudaMalloc((void**)&h->dstatus, sizeof(DevStatus)) != cudaSuccess) rc = STILES_ERR_OOM;
-  if (!rc && cudaMalloc((void**)&h->dlogdet, sizeof(double) * (h->ndiag > 0 ? h->ndiag : 1)) != cudaSuccess)
-    rc = STILES_ERR_OOM;
-  if (!rc && cudaMalloc((void**)&h->dbad, sizeof(int32_t) * (h->ndiag > 0 ? h->ndiag : 1)) != cudaSuccess)
-    rc = STILES_ERR_OOM;
+  if (!rc) rc = dev_malloc((void**)&h->dstatus, sizeof(DevStatus));
+  if (!rc) rc = dev_malloc((void**)&h->dlogdet, sizeof(double) * (h->ndiag > 0 ? h->ndiag : 1));
+  if (!rc) rc = dev_malloc((void**)&h->dbad, sizeof(int32_t) * (h->ndiag > 0 ? h->ndiag : 1));
   if (!rc && configure_persistent() != cudaSuccess) rc = STILES_ERR_CUDA;
   if (rc) {
     free_batch(h);

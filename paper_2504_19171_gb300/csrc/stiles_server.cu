@@ -89,11 +89,23 @@ struct Req {
   int64_t nt = 0, ng = 0, ns = 0, nd = 0, nr = 0;
 };
 
+// A failed allocation is reported as STILES_ERR_OOM and its error cleared
+// from the runtime's last-error slot (a later launch check must not see it).
 template <typename T>
 int dmalloc(T** p, int64_t n) {
   *p = nullptr;
   if (n <= 0) n = 1;
-  return cudaMalloc((void**)p, sizeof(T) * (size_t)n) == cudaSuccess ? 0 : STILES_ERR_OOM;
+  if (cudaMalloc((void**)p, sizeof(T) * (size_t)n) == cudaSuccess) return 0;
+  *p = nullptr;
+  cudaGetLastError();
+  return STILES_ERR_OOM;
+}
+
+inline int host_alloc(void** p, size_t bytes, unsigned flags) {
+  if (cudaHostAlloc(p, bytes, flags) == cudaSuccess) return 0;
+  *p = nullptr;
+  cudaGetLastError();
+  return STILES_ERR_OOM;
 }
 
 inline int64_t reloc(int64_t ref, int64_t add) { return ref < 0 ? ref : ref + add; }
@@ -251,14 +263,13 @@ extern "C" int stiles_server_create(int nshapes, const int* nt, const int* b, co
   if (!rc) rc = dmalloc(&h->ring_slots, 3 * (int64_t)ring);
   if (!rc) rc = dmalloc(&h->ring_ctr, 3 * 32);
   if (!rc) rc = dmalloc(&h->dstatus, 1);
-  if (!rc && cudaHostAlloc((void**)&h->ctl_host, sizeof(ServeCtl), cudaHostAllocMapped) != cudaSuccess)
-    rc = STILES_ERR_OOM;
+  if (!rc) rc = host_alloc((void**)&h->ctl_host, sizeof(ServeCtl), cudaHostAllocMapped);
   if (!rc && cudaHostGetDevicePointer((void**)&h->ctl_dev, h->ctl_host, 0) != cudaSuccess) rc = STILES_ERR_CUDA;
   if (!rc) {
     h->stage_bytes = (size_t)max_tasks * (sizeof(Task) + 5 * sizeof(int32_t) + 4) + (size_t)max_segs * sizeof(Seg) +
                      (size_t)max_succ * sizeof(int32_t) + (size_t)max_roots * sizeof(int32_t) +
                      (size_t)max_diag * sizeof(int32_t) + 4096;
-    if (cudaHostAlloc((void**)&h->stage, h->stage_bytes, cudaHostAllocDefault) != cudaSuccess) rc = STILES_ERR_OOM;
+    rc = host_alloc((void**)&h->stage, h->stage_bytes, cudaHostAllocDefault);
   }
   if (!rc && (cudaStreamCreateWithFlags(&h->kstream, cudaStreamNonBlocking) != cudaSuccess ||
               cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess))
